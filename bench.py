@@ -1,0 +1,378 @@
+"""Benchmark: BA-GMRES iterations/s and A, B Gsamples/s on the 256^3
+cone-beam scan (360 views, 384x256 detector, Poisson data from 1e5 photons,
+B = ramp-filtered voxel-driven back-projector, 40 iterations, Krylov basis
+of 41 FP32 volumes on the device).
+
+One step = one complete 40-iteration BA-GMRES solve through the C-ABI
+(r0 = B b, then per iteration A, F, B_un, the MGS sweep and the FP64 Givens
+update, then x = V y).  `value` counts Arnoldi iterations per second over
+all ranks; the inputs are resident on the device when the timed region
+starts.  `e2e` is the same metric with the data copied from pinned host
+memory before each solve and the image copied back after it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank solves its own copy of the workload (replicas,
+weak scaling) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import ct_inputs as ci  # noqa: E402
+
+METRIC = "BA-GMRES iter/s and A,B Gsamples/s at 256³ cone-beam; rel. err vs FP64 oracle"
+UNIT = "iter/s"
+K_ITERS = 40
+B_KIND = "fbp"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=ci.CONE_256.name)
+    ap.add_argument("--iters", type=int, default=K_ITERS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, on a bounded sample of one
+# BA-GMRES iteration of the same workload, extrapolated per iteration.
+# ---------------------------------------------------------------------------
+def oracle_iteration_sample(spec, x_true, b, k, frac=1.0 / 48, seed=5):
+    import oracle
+    threads = oracle.num_threads()
+    rays = ci.sample_indices(spec.m, max(1, int(spec.m * frac)), seed=seed)
+    vox = ci.sample_indices(spec.n, max(1, int(spec.n * frac)), seed=seed + 1)
+    rows = ci.sample_indices(spec.n_views * spec.nv, max(1, int(spec.n_views * spec.nv * frac)), seed=seed + 2)
+    x64 = np.ascontiguousarray(x_true, dtype=np.float64).reshape(-1)
+    b64 = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
+    t0 = time.perf_counter()
+    a_vals = oracle.project_A_rays(spec, x64, rays)
+    t1 = time.perf_counter()
+    f_rows = oracle.ramp_F_rows(spec, b64, rows)
+    t2 = time.perf_counter()
+    b_vals = oracle.backproject_B_voxels(spec, b64, vox)
+    t3 = time.perf_counter()
+    # one MGS pass of the numpy oracle (dot + axpy on full FP64 image vectors)
+    q = np.ones(spec.n)
+    v = np.full(spec.n, 0.5)
+    t4 = time.perf_counter()
+    h = float(np.dot(q, v))
+    q -= h * v
+    t5 = time.perf_counter()
+    passes = (k + 1) / 2.0 + 1.0          # average MGS passes per iteration over k iterations
+    per_iter = ((t1 - t0) / rays.size * spec.m + (t2 - t1) / rows.size * (spec.n_views * spec.nv)
+                + (t3 - t2) / vox.size * spec.n + (t5 - t4) * passes)
+    sample = ("FP64 oracle on 1/%d of one iteration at %s: A on %d rays, F on %d detector rows, "
+              "B_un on %d voxels, one numpy MGS pass; extrapolated to a full iteration"
+              % (round(1 / frac), spec.name, rays.size, rows.size, vox.size))
+    return dict(sec_per_iter=per_iter, cores=threads, sample=sample, cpu_seconds=t5 - t0,
+                rays=rays, a_vals=a_vals, vox=vox, b_vals=b_vals, rows=rows, f_rows=f_rows)
+
+
+def make_inputs(spec, seed=0):
+    x_true, _ = ci.phantom(spec, seed=seed)
+    return x_true
+
+
+def rel_err(a, b):
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index)
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _peak_hbm(peaks):
+    for key in ("hbm_gbs", "hbm_GBps", "hbm_copy_gbs", "hbm"):
+        v = peaks.get(key)
+        if isinstance(v, (int, float)):
+            return float(v)
+        if isinstance(v, dict):
+            for kk in ("gbs", "value", "burst"):
+                if isinstance(v.get(kk), (int, float)):
+                    return float(v[kk])
+    return 6800.0
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    """The oracle (FP64 CPU) as it stands, on bounded samples of the workload."""
+    if rank != 0:
+        return
+    spec = ci.WORKLOADS[args.workload]
+    x_true = make_inputs(spec)
+    import oracle
+    b = oracle.project_A_rays(spec, x_true.astype(np.float64), np.arange(0))  # warm the library
+    del b
+    # data: oracle A on the sampled rays only is not enough for B; use a
+    # synthetic smooth sinogram of the right shape for the sampled B/F work
+    sino = ci.random_vector(spec.m, seed=7, positive=True).astype(np.float32)
+    times = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        last = oracle_iteration_sample(spec, x_true, sino, args.iters, frac=1.0 / 256, seed=11 + i)
+        if i >= args.warmup:
+            times.append(last["sec_per_iter"])
+    sec = statistics.median(times)
+    value = 1.0 / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * args.iters * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": spec.name, "iters_per_step": args.iters,
+                                            "b_kind": B_KIND},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2201_07408_gb300 import ct
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    spec = ci.WORKLOADS[args.workload]
+    g = ct.Geometry.from_spec(spec, device=dev)
+    x_true = make_inputs(spec)
+    x_true_d = torch.from_numpy(x_true).to(dev)
+    p = ct.project_A(g, x_true_d)
+    torch.cuda.synchronize()
+    b_host = ci.poisson_log_data(p.cpu().numpy(), i0=1e5, seed=1)
+    b = torch.from_numpy(b_host).to(dev)
+    k = args.iters
+    opts = ct.make_opts(b_kind=B_KIND)
+    ws_bytes = ct.ct_workspace_bytes(g, k, ct.CT_SOLVER_BA, opts)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    opts.workspace = ws.data_ptr()
+    opts.workspace_bytes = ws_bytes
+    x = torch.empty(spec.vol_shape, dtype=torch.float32, device=dev)
+
+    def step():
+        return ct.ct_bagmres_solve(g, b, k, x, opts, workspace=None)
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    ct.profile_reset()
+    ct.profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    iters_done = 0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            res = step()
+            iters_done += res.iters
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ct.profile_enable(False)
+    prof = ct.profile_read()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+    tot = torch.tensor([float(iters_done)], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.SUM)
+    elapsed_max = float(t.item())
+    value = float(tot.item()) / elapsed_max
+    clocks = clk.summary()
+
+    # per-kernel figures from the library's event pairs over the timed region
+    def avg(kind):
+        ms, cnt = prof.get(kind, (0.0, 0))
+        return (ms / cnt if cnt else float("nan")), cnt
+    a_ms, a_cnt = avg("joseph_A")
+    b_ms, b_cnt = avg("voxel_B")
+    f_ms, f_cnt = avg("ramp_F")
+    mgs_ms, mgs_cnt = avg("mgs_pass")
+    a_samples = spec.joseph_samples()
+    b_samples = spec.voxel_view_samples()
+    a_gs = a_samples / (a_ms * 1e-3) / 1e9
+    b_gs = b_samples / (b_ms * 1e-3) / 1e9
+    launches = sum(c for _, c in prof.values())
+    kernel_ms = {kk: round(v[0] / max(args.steps, 1), 3) for kk, v in prof.items() if v[1]}
+
+    # e2e: host data in, image out, every step
+    b_pin = torch.from_numpy(b_host).pin_memory()
+    x_pin = torch.empty(spec.vol_shape, dtype=torch.float32).pin_memory()
+    b_e2e = torch.empty_like(b)
+    steps_e2e = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it_e2e = 0
+    for _ in range(steps_e2e):
+        b_e2e.copy_(b_pin, non_blocking=True)
+        r = ct.ct_bagmres_solve(g, b_e2e, k, x, opts, workspace=None)
+        x_pin.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        it_e2e += r.iters
+    e2e_sec = time.perf_counter() - t0
+    e2e_value = it_e2e / e2e_sec * world
+
+    # roofline of the dominant kernel ("Roofline")
+    peaks, peak_src = measured_peaks()
+    hbm_peak = _peak_hbm(peaks)
+    dom = max(("joseph_A", a_ms), ("voxel_B", b_ms), key=lambda t: t[1])
+    # compulsory DRAM bytes of one launch: the gathered array once plus the output
+    if dom[0] == "joseph_A":
+        alg_bytes = 4.0 * (spec.n + spec.m)
+        dom_ms = a_ms
+    else:
+        alg_bytes = 4.0 * (spec.n + spec.m)
+        dom_ms = b_ms
+    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
+    # FP32 issue-rate roofline of the same kernel: ~12 flops per sample
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * 2070e6 / 1e12
+    flops = 12.0 * (a_samples if dom[0] == "joseph_A" else b_samples)
+    alu_achieved = flops / (dom_ms * 1e-3) / 1e12
+    roofline = {"kernel": dom[0], "bound": "alu", "achieved": round(alu_achieved, 3),
+                "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(alu_achieved / fp32_peak, 4),
+                "traffic": None, "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x 2070 MHz" % sms,
+                "hbm": {"achieved_gbs": round(achieved, 1), "peak_gbs": hbm_peak, "peak_source": peak_src,
+                        "frac": round(achieved / hbm_peak, 4), "alg_bytes": alg_bytes}}
+
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(elapsed_max / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: 12 seeded ellipsoids, Poisson(1e5) -log data",
+            "config": {"workload": spec.name, "voxels": list(spec.vol_shape), "views": spec.n_views,
+                       "detector": [spec.nv, spec.nu], "b_kind": B_KIND, "iters_per_step": k,
+                       "basis_bytes": (k + 1) * spec.n * 4, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2: each step streams a %.2f GB Krylov basis"
+                             % ((k + 1) * spec.n * 4 / 1e9)},
+            "A_gsamples_per_s": round(a_gs, 3), "B_gsamples_per_s": round(b_gs, 3),
+            "kernel_ms_per_step": kernel_ms, "resid_final_rel": float(res.resid[res.iters] / res.resid[0]),
+            "clocks": clocks, "gpu_launches": int(launches), "roofline": roofline,
+            "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": int(spec.m * 4),
+                    "d2h_bytes_per_step": int(spec.n * 4 + (k + 1) * 8)}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_iteration_sample(spec, x_true, b_host, k)
+        # relative error of the GPU operators on the oracle's samples
+        a_gpu = p.reshape(-1)[torch.from_numpy(cb["rays"]).to(dev)].double().cpu().numpy()
+        bu = ct.backproject_B(g, b, "un").reshape(-1)[torch.from_numpy(cb["vox"]).to(dev)]
+        fr = ct.ramp_F(g, b).reshape(-1, spec.nu)[torch.from_numpy(cb["rows"]).to(dev)]
+        line["rel_err_vs_oracle"] = {"A": rel_err(a_gpu, cb["a_vals"]),
+                                     "B_un": rel_err(bu.double().cpu().numpy(), cb["b_vals"]),
+                                     "F": rel_err(fr.double().cpu().numpy(), cb["f_rows"])}
+        line["cpu_baseline"] = {"value": round(1.0 / cb["sec_per_iter"], 6), "unit": UNIT, "cores": cb["cores"],
+                                "kind": "oracle", "sample": cb["sample"],
+                                "cpu_seconds": round(cb["cpu_seconds"], 2)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * ct.h -- C-ABI of libct, the GB300 (sm_103a) CUDA library for CT
+ * reconstruction with an unmatched projector/back-projector pair by
+ * BA-GMRES and AB-GMRES (Sidky, Hansen, Jorgensen & Pan, arXiv 2201.07408).
+ *
+ * Model (Sec. I, Eq. 1): A x = b, A is m x n (m detector readings, n voxels).
+ * Square systems solved by GMRES (Sec. II): B A x = B b (Eq. 5, BA-GMRES) and
+ * A B y = b, x = B y (Eq. 4, AB-GMRES), from a zero initial vector; CGLS
+ * (Eqs. 2-3) for comparison.
+ *
+ * Conventions shared by every entry point
+ *   - Vectors are caller-owned, contiguous DEVICE buffers on the device that
+ *     was current when the geometry was created.  Volumes are vol[z][y][x]
+ *     (x fastest, n = nx*ny*nz elements); sinograms are sino[view][v][u]
+ *     (u fastest, m = n_views*nv*nu elements).  Element type: float (FP32).
+ *     A buffer may not alias another buffer of the same call.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Operator
+ *     calls are asynchronous and stream-ordered; solver calls return after
+ *     their result and residual history are complete (they synchronise the
+ *     stream once at the end).
+ *   - Scratch memory: operator calls and solvers take their temporary device
+ *     memory from the stream-ordered allocator (cudaMallocAsync on `stream`)
+ *     and release it before returning, unless the solver options supply a
+ *     workspace.
+ *   - Errors: every call returns a ct_status; on failure the outputs are
+ *     unspecified (except CT_BREAKDOWN_LUCKY, whose outputs are valid) and
+ *     ct_last_error() gives a message for the calling thread.  No call
+ *     aborts the process.
+ *
+ * Geometry (lengths in mm, angles in radians): voxel (i,j,k) centre is
+ * ((i-(nx-1)/2) vox, (j-(ny-1)/2) vox, (k-(nz-1)/2) vox); view s is at angle
+ * theta_s = angle_start + s*angle_span/n_views.  Cone beam: source at
+ * sod (cos, sin, 0), flat detector at distance sdd from the source with
+ * axes e_u = (-sin, cos, 0), e_v = (0, 0, 1); pixel (iu, iv) centre at
+ * u = (iu-(nu-1)/2) du, v = (iv-(nv-1)/2) dv.  2D parallel beam (nz = nv = 1):
+ * ray iu is the line u e_u + t e_d, e_u = (cos, sin), e_d = (-sin, cos).
+ */
+#ifndef CT_H
+#define CT_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define CT_API __attribute__((visibility("default")))
+#else
+#define CT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CT_OK = 0,
+    CT_EINVAL = 1,          /* invalid argument (sizes, pointers, options) */
+    CT_ENOMEM = 2,          /* device allocation or workspace too small */
+    CT_ECUDA = 3,           /* a CUDA runtime call failed */
+    CT_ENONFINITE = 4,      /* a norm became NaN/Inf during a solve */
+    CT_ETIMEOUT = 5,        /* a bounded device wait gave up */
+    CT_BREAKDOWN_LUCKY = 6  /* informational: the Krylov space became invariant;
+                               the returned solution is exact and valid */
+} ct_status;
+
+typedef enum { CT_PARALLEL_2D = 0, CT_CONE_3D = 1 } ct_geom_kind;
+
+typedef enum { CT_F32 = 0, CT_BF16 = 1 } ct_dtype;
+
+/* Which back-projector B a call uses (Sec. III). */
+typedef enum {
+    CT_B_UN = 0,   /* B_un: voxel-driven back-projection, bilinear detector interpolation */
+    CT_B_FBP = 1,  /* B_FBP = B_un F: ramp-filtered (FDK-weighted) back-projection */
+    CT_B_AT = 2    /* the exact transpose A^T (matched pair; CGLS reference) */
+} ct_b_kind;
+
+typedef enum { CT_SOLVER_BA = 0, CT_SOLVER_AB = 1, CT_SOLVER_CGLS = 2 } ct_solver;
+
+typedef struct {
+    int kind;                  /* ct_geom_kind */
+    int nx, ny, nz;            /* voxels; 2D parallel beam needs nz = 1 */
+    double voxel_mm;           /* voxel edge */
+    int n_views;
+    double angle_start_rad;    /* theta_0 */
+    double angle_span_rad;     /* views at theta_0 + s*span/n_views */
+    int nu, nv;                /* detector pixels; 2D parallel beam needs nv = 1 */
+    double du_mm, dv_mm;       /* pixel pitch */
+    double sod_mm, sdd_mm;     /* source-axis and source-detector distances (cone only) */
+    int vol_dtype;             /* ct_dtype of basis/volume storage; CT_F32 */
+    int sino_dtype;            /* ct_dtype of sinogram storage; CT_F32 */
+} ct_geom_desc;
+
+typedef struct ct_geom ct_geom;
+
+typedef struct {
+    int b_kind;              /* ct_b_kind; default CT_B_UN */
+    double tol;              /* stop when resid[j] <= tol*resid[0]; 0 = run all k */
+    int dot_mode;            /* Arnoldi inner products: 0 = FP32 with compensated (two-sum)
+                                accumulation, 1 = FP32 products, FP64 reduction (default) */
+    int reorth;              /* 0 = one MGS sweep (default), 1 = a second sweep when the
+                                norm drops below 1/sqrt(2) of its value before the sweep */
+    int record_data_resid;   /* CGLS only: resid holds the recomputed ||b - A x_j|| */
+    void *workspace;         /* optional caller device buffer (NULL = library allocates) */
+    size_t workspace_bytes;  /* its size; must be >= ct_workspace_bytes(...) */
+} ct_solve_opts;
+
+/* Fills `opts` with the defaults listed above. */
+CT_API void ct_solve_opts_default(ct_solve_opts *opts);
+
+/* Creates a geometry handle on the current device: validates the
+ * description (positive sizes, 2D needs nz = nv = 1, cone needs
+ * sdd > sod > 0 and the volume inside the source circle, FP32 dtypes) and
+ * uploads per-view tables.  The library owns the handle; free it with
+ * ct_geom_destroy.  Returns CT_EINVAL or CT_ECUDA on failure (*out = NULL). */
+CT_API ct_status ct_geom_create(const ct_geom_desc *desc, ct_geom **out);
+
+/* Frees the handle and its device tables (NULL is a no-op). */
+CT_API void ct_geom_destroy(ct_geom *geom);
+
+/* Number of voxels n and of detector readings m of a geometry. */
+CT_API size_t ct_geom_n(const ct_geom *geom);
+CT_API size_t ct_geom_m(const ct_geom *geom);
+
+/* y = A x: ray-driven projector (Sec. I Eq. 1; Sec. III "ray-driven
+ * cone-beam projector").  Read as Joseph's method: for each ray, one
+ * bilinear sample on every voxel-centre plane of the ray's dominant axis
+ * (x when |d_x| >= |d_y|), neighbours outside the grid count as zero, sum
+ * times the step vox*|d|/|d_a|.  x: n floats, y: m floats (overwritten). */
+CT_API ct_status ct_project_A(const ct_geom *geom, const float *x_dev, float *y_dev, void *stream);
+
+/* x = B y: back-projection (Sec. III).  b_kind CT_B_UN: voxel-driven
+ * back-projection with bilinear detector interpolation, weight
+ * vox^3 M^2/(du dv) (M = sdd/depth; 2D: vox^2/du).  CT_B_FBP: B_un F, F the
+ * ramp filter (cosine weight, Ram-Lak row convolution, FBP scaling).
+ * CT_B_AT: the exact transpose A^T.  y: m floats, x: n floats (overwritten). */
+CT_API ct_status ct_backproject_B(const ct_geom *geom, const float *y_dev, float *x_dev, int b_kind,
+                           void *stream);
+
+/* x = A^T y: exact transpose of ct_project_A (normal equations, Sec. I
+ * Eq. 3).  Scatter with FP32 atomics: the summation order varies between
+ * runs.  y: m floats, x: n floats (overwritten). */
+CT_API ct_status ct_adjoint_At(const ct_geom *geom, const float *y_dev, float *x_dev, void *stream);
+
+/* y = B^T x: exact transpose of ct_backproject_B for b_kind CT_B_UN
+ * (voxel splatting with the same bilinear weights) and CT_B_FBP
+ * (F^T B_un^T); CT_B_AT gives A x.  FP32 atomics.  x: n, y: m (overwritten). */
+CT_API ct_status ct_adjoint_Bt(const ct_geom *geom, const float *x_dev, float *y_dev, int b_kind,
+                        void *stream);
+
+/* yf = F y (transpose = 0) or yf = F^T y (transpose = 1): the ramp filter
+ * of B_FBP = B_un F (Sec. III) on its own.  y, yf: m floats, distinct. */
+CT_API ct_status ct_ramp_F(const ct_geom *geom, const float *y_dev, float *yf_dev, int transpose,
+                    void *stream);
+
+/* BA-GMRES (Sec. II, Eq. 5): k iterations on B A x = B b from x0 = 0, with
+ * the Krylov basis (k+1 image-space vectors, FP32) held on the device,
+ * modified Gram-Schmidt Arnoldi, FP64 Givens least squares.
+ *   b_dev:      m floats (data).
+ *   k:          iteration count >= 1 (the method's only parameter, Sec. I).
+ *   x_out_dev:  n floats, the iterate x_j after the last iteration done.
+ *   resid_hist: HOST array of k+1 doubles: resid[0] = ||B b||,
+ *               resid[j] = ||B b - B A x_j|| (non-increasing); entries after
+ *               the last iteration done are set to -1.  May be NULL.
+ *   opts:       NULL = defaults.
+ *   iters_done: iterations performed (< k after a tolerance stop or a lucky
+ *               breakdown).  May be NULL.
+ * Returns CT_BREAKDOWN_LUCKY (solution valid) when the Krylov space became
+ * invariant, CT_ENONFINITE when a norm was NaN/Inf. */
+CT_API ct_status ct_bagmres_solve(const ct_geom *geom, const float *b_dev, int k, float *x_out_dev,
+                           double *resid_hist, const ct_solve_opts *opts, int *iters_done,
+                           void *stream);
+
+/* AB-GMRES (Sec. II, Eq. 4): k iterations on A B y = b from y0 = 0 with the
+ * basis in data space (k+1 sinogram-size vectors), x = B y.
+ * resid[0] = ||b||, resid[j] = ||b - A x_j||.  Arguments as ct_bagmres_solve. */
+CT_API ct_status ct_abgmres_solve(const ct_geom *geom, const float *b_dev, int k, float *x_out_dev,
+                           double *resid_hist, const ct_solve_opts *opts, int *iters_done,
+                           void *stream);
+
+/* CGLS (Sec. I, Eqs. 2-3) with back-projector opts->b_kind in place of A^T
+ * (CT_B_AT gives the textbook method; CT_B_UN shows the divergence of
+ * Sec. III).  resid[j] = ||r_j|| of the recursively updated residual, or the
+ * recomputed ||b - A x_j|| when opts->record_data_resid is set (one more A
+ * per iteration).  Arguments as ct_bagmres_solve. */
+CT_API ct_status ct_cgls_solve(const ct_geom *geom, const float *b_dev, int k, float *x_out_dev,
+                        double *resid_hist, const ct_solve_opts *opts, int *iters_done,
+                        void *stream);
+
+/* Device workspace in bytes that a solve with these arguments needs when
+ * the caller supplies it through ct_solve_opts (solver: ct_solver). */
+CT_API size_t ct_workspace_bytes(const ct_geom *geom, int k, int solver, const ct_solve_opts *opts);
+
+/* One modified Gram-Schmidt sweep of the Arnoldi process (Sec. II: the
+ * new Krylov vector is orthonormalised against the basis).  For
+ * i = 0..j-1: h[i] = <q, V_i>; q -= h[i] V_i; then h[j] = ||q||.
+ *   V_dev: j vectors of len floats, vector i at V_dev + i*ldv (ldv >= len).
+ *   q_dev: len floats, updated in place (not normalised).
+ *   h_dev: DEVICE array of j+1 doubles (output).
+ * dot_mode as in ct_solve_opts.  Stream-ordered, asynchronous. */
+CT_API ct_status ct_mgs_sweep(const float *V_dev, size_t ldv, int j, size_t len, float *q_dev,
+                       double *h_dev, int dot_mode, void *stream);
+
+/* x = sum_i y[i] V_i for i < k (the GMRES update x_k = V_k y_k, Sec. II).
+ * y_dev: DEVICE array of k doubles.  Stream-ordered, asynchronous. */
+CT_API ct_status ct_basis_combine(const float *V_dev, size_t ldv, int k, size_t len,
+                           const double *y_dev, float *x_dev, void *stream);
+
+/* Per-kernel timing (no counterpart in the paper; instrumentation for
+ * measurement).  ct_profile_enable(1) makes every kernel launch of the
+ * library record a CUDA event pair on its stream; ct_profile_read waits for
+ * the recorded pairs and writes, per kernel kind (index < the returned
+ * count, names from ct_profile_kind_name), the accumulated device
+ * milliseconds and launch counts since the last ct_profile_reset.  Either
+ * output may be NULL.  Process-wide, thread-safe. */
+CT_API void ct_profile_enable(int on);
+CT_API void ct_profile_reset(void);
+CT_API int ct_profile_read(double *ms_out, long long *launches_out, int max_kinds);
+CT_API const char *ct_profile_kind_name(int kind);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+CT_API const char *ct_last_error(void);
+
+/* Library version string. */
+CT_API const char *ct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CT_H */

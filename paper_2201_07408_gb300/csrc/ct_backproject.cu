@@ -1,0 +1,325 @@
+// Voxel-driven back-projector B_un, ramp filter F (B_FBP = B_un F) and the
+// exact transposes B_un^T, F^T (Sec. III).
+//
+// B_un: for every voxel and view, the voxel centre is projected from the
+// source onto the detector (depth W, magnification M = sdd/W, u = M t,
+// v = M z), the detector value there is interpolated bilinearly (zero
+// outside) and accumulated with weight kB M^2.
+//
+// GPU layout.  One thread owns a column (x, y) and a run of ZC consecutive
+// z; per view it computes W, M, u and the u-interpolation weights once and
+// then walks its z run with v affine in z.  The sinogram is read from a
+// copy with zero borders (PAD_U pixels along u, PAD_V rows along v): a view
+// whose u footprint misses the detector is skipped, and clamping the row
+// index into the border makes every other gather in bounds.
+#include <algorithm>
+
+#include "ct_internal.cuh"
+
+namespace ct {
+
+// ---------------------------------------------------------------------------
+// Plain -> padded sinogram copy (optionally scaled, optionally normalising
+// the source in place).
+// ---------------------------------------------------------------------------
+__global__ void pad_sino_kernel(GeomDev g, float *__restrict__ src, const double *__restrict__ scale,
+                                int normalize_inplace, float *__restrict__ dst,
+                                const int *__restrict__ stop)
+{
+    if (stop && *stop) return;
+    const size_t total = size_t(g.n_views) * g.nvp * g.pitchU;
+    const float sc = scale ? float(*scale) : 1.0f;
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < total;
+         i += size_t(gridDim.x) * blockDim.x) {
+        const int up = int(i % g.pitchU);
+        const size_t t = i / g.pitchU;
+        const int vp = int(t % g.nvp);
+        const int s = int(t / g.nvp);
+        const int u = up - PAD_U, v = vp - PAD_V;
+        float val = 0.0f;
+        if (u >= 0 && u < g.nu && v >= 0 && v < g.nv) {
+            const size_t si = (size_t(s) * g.nv + v) * g.nu + u;
+            val = src[si] * sc;
+            if (normalize_inplace) src[si] = val;
+        }
+        dst[i] = val;
+    }
+}
+
+cudaError_t launch_pad_sino(const GeomDev &g, float *src, const double *scale, bool normalize_inplace,
+                            float *dst, const int *stop, cudaStream_t st)
+{
+    const size_t total = size_t(g.n_views) * g.nvp * g.pitchU;
+    unsigned blocks = unsigned(std::min<size_t>((total + 255) / 256, size_t(num_sms()) * 16));
+    ProfScope prof(PK_PAD_SINO, st);
+    pad_sino_kernel<<<blocks, 256, 0, st>>>(g, src, scale, normalize_inplace ? 1 : 0, dst, stop);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Ramp filter.  One block per detector row: the cosine-weighted row sits in
+// shared memory between nu zeros on either side, so the linear convolution
+// with the (symmetric, odd-tap) Ram-Lak kernel needs no bounds tests.
+// F^T applies the cosine weight after the convolution instead of before.
+// ---------------------------------------------------------------------------
+constexpr int RAMP_BLOCK = 128;
+
+__device__ __forceinline__ float cosine_weight(const GeomDev &g, int iu, int iv)
+{
+    if (g.kind != CT_CONE_3D) return 1.0f;
+    const float u = (float(iu) - g.cu) * g.du;
+    const float v = (float(iv) - g.cv) * g.dv;
+    return g.sdd / sqrtf(fmaf(g.sdd, g.sdd, fmaf(u, u, v * v)));
+}
+
+__global__ void __launch_bounds__(RAMP_BLOCK) ramp_kernel(GeomDev g, const float *__restrict__ src,
+                                                          float *__restrict__ dst, SinoLayout lay,
+                                                          int transpose,
+                                                          const int *__restrict__ stop)
+{
+    if (stop && *stop) return;
+    extern __shared__ float sm[];
+    const int nu = g.nu;
+    float *row = sm;            // 3 nu: [zeros | weighted row | zeros]
+    float *taps = sm + 3 * nu;  // nu
+    const int r = blockIdx.x;   // s*nv + iv
+    const int iv = r % g.nv;
+    const int s = r / g.nv;
+    const float *in = src + size_t(r) * nu;
+    for (int i = threadIdx.x; i < nu; i += RAMP_BLOCK) {
+        const float w = transpose ? 1.0f : cosine_weight(g, i, iv);
+        row[i] = 0.0f;
+        row[nu + i] = in[i] * w;
+        row[2 * nu + i] = 0.0f;
+        taps[i] = g.ramp_taps[i];
+    }
+    __syncthreads();
+    float *out = dst + (size_t(s) * lay.rows_per_view + iv + lay.row_off) * lay.pitch + lay.col_off;
+    for (int i = threadIdx.x; i < nu; i += RAMP_BLOCK) {
+        const float *c = row + nu + i;
+        float acc = taps[0] * c[0];
+        for (int k = 1; k < nu; k += 2) acc = fmaf(taps[k], c[-k] + c[k], acc);
+        out[i] = transpose ? acc * cosine_weight(g, i, iv) : acc;
+    }
+}
+
+cudaError_t launch_ramp(const GeomDev &g, const float *src, float *dst, SinoLayout lay, bool transpose,
+                        const int *stop, cudaStream_t st)
+{
+    const size_t smem = size_t(4) * g.nu * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(ramp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(smem));
+        if (e != cudaSuccess) return e;
+    }
+    ProfScope prof(PK_RAMP, st);
+    ramp_kernel<<<g.n_views * g.nv, RAMP_BLOCK, smem, st>>>(g, src, dst, lay, transpose ? 1 : 0, stop);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// x = B_un y.
+// ---------------------------------------------------------------------------
+constexpr int B_BX = 32, B_BY = 4;
+
+struct ColumnView {
+    int skip;       // the u footprint misses the detector
+    int col;        // padded column offset of the left neighbour
+    float a0, a1;   // weight * (1 - wu), weight * wu
+    float fv0, gv;  // v fractional index of the first z of the run, slope per z
+};
+
+__device__ __forceinline__ ColumnView column_view(const GeomDev &g, int s, float x, float y, float zfirst)
+{
+    const float4 *vp = reinterpret_cast<const float4 *>(g.viewB + s);
+    const float4 p = __ldg(vp), q = __ldg(vp + 1);
+    // p = (w0, wx, wy, tx), q = (ty, mnum, -, -)
+    const float W = fmaf(x, p.y, fmaf(y, p.z, p.x));
+    const float t = fmaf(x, p.w, y * q.x);
+    const float M = q.y / W;
+    const float fu = fmaf(M * t, g.inv_du, g.cu);
+    const float u0f = floorf(fu);
+    const float wu = fu - u0f;
+    ColumnView c;
+    const int u0 = int(fmaxf(fminf(u0f, float(g.nu + 1)), -2.0f));
+    c.skip = (u0 < -1) || (u0 > g.nu - 1);
+    c.col = u0 + PAD_U;
+    const float w = g.kB * M * M;
+    c.a0 = w * (1.0f - wu);
+    c.a1 = w * wu;
+    c.gv = M * g.vox * g.inv_dv;
+    c.fv0 = fmaf(M * zfirst, g.inv_dv, g.cv);
+    return c;
+}
+
+template <int ZC>
+__global__ void __launch_bounds__(B_BX *B_BY) voxel_B_kernel(GeomDev g, const float *__restrict__ ypad,
+                                                             float *__restrict__ x,
+                                                             const int *__restrict__ stop)
+{
+    if (stop && *stop) return;
+    const int ix = blockIdx.x * B_BX + threadIdx.x;
+    const int iy = blockIdx.y * B_BY + threadIdx.y;
+    const int iz0 = blockIdx.z * ZC;
+    if (ix >= g.nx || iy >= g.ny) return;
+    const float xc = (float(ix) - g.cx) * g.vox;
+    const float yc = (float(iy) - g.cy) * g.vox;
+    const float zfirst = (float(iz0) - g.cz) * g.vox;
+    const int view_stride = g.nvp * g.pitchU;
+    float acc[ZC];
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) acc[k] = 0.0f;
+    for (int s = 0; s < g.n_views; ++s) {
+        const ColumnView c = column_view(g, s, xc, yc, zfirst);
+        if (c.skip) continue;
+        const float *vbase = ypad + size_t(s) * view_stride + c.col;
+#pragma unroll
+        for (int k = 0; k < ZC; ++k) {
+            const float fv = fmaf(float(k), c.gv, c.fv0);
+            const float v0f = floorf(fv);
+            const float wv = fv - v0f;
+            const int v0 = int(fmaxf(fminf(v0f, float(g.nv)), -2.0f));
+            const float *rowp = vbase + (v0 + PAD_V) * g.pitchU;
+            const float r0 = fmaf(c.a0, __ldg(rowp), c.a1 * __ldg(rowp + 1));
+            const float r1 = fmaf(c.a0, __ldg(rowp + g.pitchU), c.a1 * __ldg(rowp + g.pitchU + 1));
+            acc[k] += fmaf(wv, r1 - r0, r0);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) {
+        const int iz = iz0 + k;
+        if (iz < g.nz) x[(size_t(iz) * g.ny + iy) * g.nx + ix] = acc[k];
+    }
+}
+
+cudaError_t launch_voxel_B(const GeomDev &g, const float *ypad, float *x, const int *stop, cudaStream_t st)
+{
+    ProfScope prof(PK_VOXEL_B, st);
+    dim3 block(B_BX, B_BY);
+    if (g.nz == 1) {
+        dim3 grid((g.nx + B_BX - 1) / B_BX, (g.ny + B_BY - 1) / B_BY, 1);
+        voxel_B_kernel<1><<<grid, block, 0, st>>>(g, ypad, x, stop);
+    } else {
+        constexpr int ZC = 8;
+        dim3 grid((g.nx + B_BX - 1) / B_BX, (g.ny + B_BY - 1) / B_BY, (g.nz + ZC - 1) / ZC);
+        voxel_B_kernel<ZC><<<grid, block, 0, st>>>(g, ypad, x, stop);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// y += B_un^T x: voxel splatting with the same weights (FP32 atomics into
+// the plain sinogram, bounds-checked).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void splat(float *y, const GeomDev &g, int s, int iu, int iv, float val)
+{
+    if (iu < 0 || iu >= g.nu || iv < 0 || iv >= g.nv || val == 0.0f) return;
+    atomicAdd(y + (size_t(s) * g.nv + iv) * g.nu + iu, val);
+}
+
+__global__ void __launch_bounds__(B_BX *B_BY) voxel_Bt_kernel(GeomDev g, const float *__restrict__ x,
+                                                              float *__restrict__ y,
+                                                              const int *__restrict__ stop)
+{
+    if (stop && *stop) return;
+    const int ix = blockIdx.x * B_BX + threadIdx.x;
+    const int iy = blockIdx.y * B_BY + threadIdx.y;
+    const int iz = blockIdx.z;
+    if (ix >= g.nx || iy >= g.ny) return;
+    const float xv = x[(size_t(iz) * g.ny + iy) * g.nx + ix];
+    if (xv == 0.0f) return;
+    const float xc = (float(ix) - g.cx) * g.vox;
+    const float yc = (float(iy) - g.cy) * g.vox;
+    const float zc = (float(iz) - g.cz) * g.vox;
+    for (int s = 0; s < g.n_views; ++s) {
+        const ColumnView c = column_view(g, s, xc, yc, zc);
+        if (c.skip) continue;
+        const float fv = c.fv0;
+        const float v0f = floorf(fv);
+        const float wv = fv - v0f;
+        if (v0f < -1.0f || v0f > float(g.nv - 1)) continue;
+        const int v0 = int(v0f);
+        const int u0 = c.col - PAD_U;
+        splat(y, g, s, u0, v0, xv * c.a0 * (1.0f - wv));
+        splat(y, g, s, u0 + 1, v0, xv * c.a1 * (1.0f - wv));
+        splat(y, g, s, u0, v0 + 1, xv * c.a0 * wv);
+        splat(y, g, s, u0 + 1, v0 + 1, xv * c.a1 * wv);
+    }
+}
+
+cudaError_t launch_voxel_Bt(const GeomDev &g, const float *x, float *y, const int *stop, cudaStream_t st)
+{
+    dim3 block(B_BX, B_BY);
+    dim3 grid((g.nx + B_BX - 1) / B_BX, (g.ny + B_BY - 1) / B_BY, g.nz);
+    ProfScope prof(PK_VOXEL_BT, st);
+    voxel_Bt_kernel<<<grid, block, 0, st>>>(g, x, y, stop);
+    return cudaGetLastError();
+}
+
+}  // namespace ct
+
+using namespace ct;
+
+extern "C" ct_status ct_ramp_F(const ct_geom *geom, const float *y_dev, float *yf_dev, int transpose,
+                               void *stream)
+{
+    if (!geom || !y_dev || !yf_dev) return set_error(CT_EINVAL, "ct_ramp_F: NULL argument");
+    if (y_dev == yf_dev) return set_error(CT_EINVAL, "ct_ramp_F: input and output must differ");
+    cudaError_t e = launch_ramp(geom->g, y_dev, yf_dev, plain_layout(geom->g), transpose != 0, nullptr,
+                                static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_error(e, "ct_ramp_F launch");
+    return CT_OK;
+}
+
+extern "C" ct_status ct_backproject_B(const ct_geom *geom, const float *y_dev, float *x_dev, int b_kind,
+                                      void *stream)
+{
+    if (!geom || !y_dev || !x_dev) return set_error(CT_EINVAL, "ct_backproject_B: NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (b_kind == CT_B_AT) return ct_adjoint_At(geom, y_dev, x_dev, stream);
+    if (b_kind != CT_B_UN && b_kind != CT_B_FBP)
+        return set_error(CT_EINVAL, "ct_backproject_B: unknown b_kind %d", b_kind);
+    const GeomDev &g = geom->g;
+    Arena ar;
+    ct_status rc = arena_open(ar, padded_sino_bytes(g), nullptr, 0, st);
+    if (rc != CT_OK) return rc;
+    float *ypad = ar.take<float>(size_t(g.n_views) * g.nvp * g.pitchU);
+    cudaError_t e;
+    if (b_kind == CT_B_FBP) {
+        e = cudaMemsetAsync(ypad, 0, size_t(g.n_views) * g.nvp * g.pitchU * sizeof(float), st);
+        if (e == cudaSuccess) e = launch_ramp(g, y_dev, ypad, padded_layout(g), false, nullptr, st);
+    } else {
+        e = launch_pad_sino(g, const_cast<float *>(y_dev), nullptr, false, ypad, nullptr, st);
+    }
+    if (e == cudaSuccess) e = launch_voxel_B(g, ypad, x_dev, nullptr, st);
+    arena_close(ar);
+    if (e != cudaSuccess) return cuda_error(e, "ct_backproject_B launch");
+    return CT_OK;
+}
+
+extern "C" ct_status ct_adjoint_Bt(const ct_geom *geom, const float *x_dev, float *y_dev, int b_kind,
+                                   void *stream)
+{
+    if (!geom || !x_dev || !y_dev) return set_error(CT_EINVAL, "ct_adjoint_Bt: NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (b_kind == CT_B_AT) return ct_project_A(geom, x_dev, y_dev, stream);
+    if (b_kind != CT_B_UN && b_kind != CT_B_FBP)
+        return set_error(CT_EINVAL, "ct_adjoint_Bt: unknown b_kind %d", b_kind);
+    const GeomDev &g = geom->g;
+    if (b_kind == CT_B_UN) {
+        CT_CUDA(cudaMemsetAsync(y_dev, 0, geom->m * sizeof(float), st));
+        cudaError_t e = launch_voxel_Bt(g, x_dev, y_dev, nullptr, st);
+        if (e != cudaSuccess) return cuda_error(e, "ct_adjoint_Bt launch");
+        return CT_OK;
+    }
+    Arena ar;
+    ct_status rc = arena_open(ar, Arena::align(geom->m * sizeof(float)), nullptr, 0, st);
+    if (rc != CT_OK) return rc;
+    float *tmp = ar.take<float>(geom->m);
+    cudaError_t e = cudaMemsetAsync(tmp, 0, geom->m * sizeof(float), st);
+    if (e == cudaSuccess) e = launch_voxel_Bt(g, x_dev, tmp, nullptr, st);
+    if (e == cudaSuccess) e = launch_ramp(g, tmp, y_dev, plain_layout(g), true, nullptr, st);
+    arena_close(ar);
+    if (e != cudaSuccess) return cuda_error(e, "ct_adjoint_Bt launch");
+    return CT_OK;
+}

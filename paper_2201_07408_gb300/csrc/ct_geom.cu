@@ -1,0 +1,242 @@
+// Geometry handle, per-view tables, error reporting and scratch arenas.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "ct_internal.cuh"
+
+namespace ct {
+
+static thread_local char g_err[512] = "";
+
+ct_status set_error(ct_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+ct_status cuda_error(cudaError_t e, const char *what)
+{
+    return set_error(e == cudaErrorMemoryAllocation ? CT_ENOMEM : CT_ECUDA, "%s: %s (%s)", what,
+                     cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+ct_status arena_open(Arena &a, size_t bytes, void *workspace, size_t workspace_bytes,
+                     cudaStream_t stream)
+{
+    a = Arena{};
+    a.stream = stream;
+    a.size = bytes;
+    if (bytes == 0) return CT_OK;
+    if (workspace) {
+        if (workspace_bytes < bytes)
+            return set_error(CT_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed",
+                             workspace_bytes, bytes);
+        if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
+            return set_error(CT_EINVAL, "workspace must be 256-byte aligned");
+        a.base = static_cast<char *>(workspace);
+        a.owned = false;
+        return CT_OK;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(CT_ENOMEM, "cudaMallocAsync(%zu bytes) failed: %s", bytes,
+                         cudaGetErrorString(e));
+    }
+    a.base = static_cast<char *>(p);
+    a.owned = true;
+    return CT_OK;
+}
+
+void arena_close(Arena &a)
+{
+    if (a.owned && a.base) cudaFreeAsync(a.base, a.stream);
+    a = Arena{};
+}
+
+size_t plane_copies_bytes(const GeomDev &g)
+{
+    size_t xc = size_t(g.nzp) * g.nx * g.pitchX;
+    size_t yc = size_t(g.nzp) * g.ny * g.pitchY;
+    return Arena::align(xc * sizeof(float)) + Arena::align(yc * sizeof(float));
+}
+
+size_t padded_sino_bytes(const GeomDev &g)
+{
+    return Arena::align(size_t(g.n_views) * g.nvp * g.pitchU * sizeof(float));
+}
+
+int num_sms()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        sms = 132;
+    return sms;
+}
+
+}  // namespace ct
+
+using namespace ct;
+
+extern "C" {
+
+const char *ct_last_error(void) { return ct::g_err; }
+
+const char *ct_version(void) { return "libct 0.1 (sm_103a)"; }
+
+void ct_solve_opts_default(ct_solve_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->b_kind = CT_B_UN;
+    o->tol = 0.0;
+    o->dot_mode = 1;
+    o->reorth = 0;
+    o->record_data_resid = 0;
+    o->workspace = nullptr;
+    o->workspace_bytes = 0;
+}
+
+size_t ct_geom_n(const ct_geom *geom) { return geom ? geom->n : 0; }
+size_t ct_geom_m(const ct_geom *geom) { return geom ? geom->m : 0; }
+
+ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
+{
+    if (!out) return set_error(CT_EINVAL, "ct_geom_create: out is NULL");
+    *out = nullptr;
+    if (!d) return set_error(CT_EINVAL, "ct_geom_create: desc is NULL");
+    if (d->kind != CT_PARALLEL_2D && d->kind != CT_CONE_3D)
+        return set_error(CT_EINVAL, "unknown geometry kind %d", d->kind);
+    if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0 || d->nu <= 0 || d->nv <= 0 || d->n_views <= 0)
+        return set_error(CT_EINVAL, "all grid, detector and view counts must be positive");
+    if (!(d->voxel_mm > 0) || !(d->du_mm > 0) || !(d->dv_mm > 0))
+        return set_error(CT_EINVAL, "voxel and pixel sizes must be positive");
+    if (!std::isfinite(d->angle_start_rad) || !std::isfinite(d->angle_span_rad))
+        return set_error(CT_EINVAL, "view angles must be finite");
+    if (d->vol_dtype != CT_F32 || d->sino_dtype != CT_F32)
+        return set_error(CT_EINVAL, "only CT_F32 storage is supported");
+    if (d->kind == CT_PARALLEL_2D && (d->nz != 1 || d->nv != 1))
+        return set_error(CT_EINVAL, "2D parallel beam needs nz = 1 and nv = 1");
+    if (d->kind == CT_CONE_3D) {
+        if (!(d->sod_mm > 0) || !(d->sdd_mm > d->sod_mm))
+            return set_error(CT_EINVAL, "cone beam needs sdd > sod > 0");
+        double hx = 0.5 * d->nx * d->voxel_mm, hy = 0.5 * d->ny * d->voxel_mm;
+        if (std::sqrt(hx * hx + hy * hy) >= d->sod_mm)
+            return set_error(CT_EINVAL, "the volume must lie inside the source circle");
+    }
+    // 32-bit indexing of rays, voxels and padded copies
+    const double lim = 2147483647.0;
+    double nzp = d->nz + 2.0 * PAD_A;
+    if (double(d->n_views) * d->nv * d->nu >= lim ||
+        double(d->nx) * d->ny * d->nz >= lim ||
+        nzp * d->nx * (d->ny + 2.0 * PAD_A) >= lim || nzp * d->ny * (d->nx + 2.0 * PAD_A) >= lim ||
+        double(d->n_views) * (d->nv + 2.0 * PAD_V) * (d->nu + 2.0 * PAD_U) >= lim)
+        return set_error(CT_EINVAL, "problem too large for 32-bit element indexing");
+
+    ct_geom *g = new ct_geom();
+    g->desc = *d;
+    cudaGetDevice(&g->device);
+    g->n = size_t(d->nx) * d->ny * d->nz;
+    g->m = size_t(d->n_views) * d->nv * d->nu;
+
+    GeomDev &k = g->g;
+    k.kind = d->kind;
+    k.nx = d->nx; k.ny = d->ny; k.nz = d->nz;
+    k.n_views = d->n_views; k.nu = d->nu; k.nv = d->nv;
+    k.vox = float(d->voxel_mm);
+    k.inv_vox = float(1.0 / d->voxel_mm);
+    k.du = float(d->du_mm); k.dv = float(d->dv_mm);
+    k.inv_du = float(1.0 / d->du_mm); k.inv_dv = float(1.0 / d->dv_mm);
+    k.cx = 0.5f * (d->nx - 1); k.cy = 0.5f * (d->ny - 1); k.cz = 0.5f * (d->nz - 1);
+    k.cu = 0.5f * (d->nu - 1); k.cv = 0.5f * (d->nv - 1);
+    const bool cone = d->kind == CT_CONE_3D;
+    const double vox = d->voxel_mm;
+    k.kB = float(cone ? vox * vox * vox / (d->du_mm * d->dv_mm) : vox * vox / d->du_mm);
+    k.sdd = float(cone ? d->sdd_mm : 1.0);
+    k.nzp = d->nz + 2 * PAD_A;
+    k.pitchX = d->ny + 2 * PAD_A;
+    k.pitchY = d->nx + 2 * PAD_A;
+    k.nvp = d->nv + 2 * PAD_V;
+    k.pitchU = d->nu + 2 * PAD_U;
+
+    // per-view tables (computed in double, stored in float)
+    std::vector<ViewA> va(d->n_views);
+    std::vector<ViewB> vb(d->n_views);
+    for (int s = 0; s < d->n_views; ++s) {
+        double th = d->angle_start_rad + double(s) * d->angle_span_rad / double(d->n_views);
+        double c = std::cos(th), sn = std::sin(th);
+        if (cone) {
+            double sod = d->sod_mm, sdd = d->sdd_mm;
+            va[s] = ViewA{float(-sdd * c), float(-sn), float(-sdd * sn), float(c), 1.0f,
+                          float(sod), float(sod * c), float(sod * sn)};
+            vb[s] = ViewB{float(sod), float(-c), float(-sn), float(-sn), float(c), float(sdd), 0.f, 0.f};
+        } else {
+            va[s] = ViewA{float(-sn), 0.0f, float(c), 0.0f, 0.0f, 1.0f, 0.0f, 0.0f};
+            vb[s] = ViewB{1.0f, 0.0f, 0.0f, float(c), float(sn), 1.0f, 0.f, 0.f};
+        }
+    }
+    // Ram-Lak taps of the ramp filter with the FBP scale folded in:
+    // h[0] = 1/(4 tau^2), h[odd k] = -1/(pi^2 k^2 tau^2), h[even k] = 0, times tau * c_F.
+    std::vector<float> taps(d->nu);
+    {
+        const double PI = 3.14159265358979323846;
+        double tau = cone ? d->du_mm * d->sod_mm / d->sdd_mm : d->du_mm;
+        double cf = (PI / d->n_views) *
+                    (cone ? (d->sod_mm / d->sdd_mm) * (d->sod_mm / d->sdd_mm) * d->du_mm * d->dv_mm /
+                                (vox * vox * vox)
+                          : d->du_mm / (vox * vox));
+        double scale = cf * tau;
+        for (int q = 0; q < d->nu; ++q) {
+            double h = q == 0 ? 1.0 / (4.0 * tau * tau)
+                              : (q % 2 ? -1.0 / (PI * PI * double(q) * q * tau * tau) : 0.0);
+            taps[q] = float(h * scale);
+        }
+    }
+    size_t bA = Arena::align(va.size() * sizeof(ViewA));
+    size_t bB = Arena::align(vb.size() * sizeof(ViewB));
+    size_t bT = Arena::align(taps.size() * sizeof(float));
+    cudaError_t e = cudaMalloc(&g->d_tables, bA + bB + bT);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_error(e, "cudaMalloc(geometry tables)");
+    }
+    char *base = static_cast<char *>(g->d_tables);
+    e = cudaMemcpy(base, va.data(), va.size() * sizeof(ViewA), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(base + bA, vb.data(), vb.size() * sizeof(ViewB), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(base + bA + bB, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(g->d_tables);
+        delete g;
+        return cuda_error(e, "cudaMemcpy(geometry tables)");
+    }
+    k.viewA = reinterpret_cast<const ViewA *>(base);
+    k.viewB = reinterpret_cast<const ViewB *>(base + bA);
+    k.ramp_taps = reinterpret_cast<const float *>(base + bA + bB);
+    *out = g;
+    return CT_OK;
+}
+
+void ct_geom_destroy(ct_geom *geom)
+{
+    if (!geom) return;
+    if (geom->d_tables) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(geom->device);
+        cudaFree(geom->d_tables);
+        cudaSetDevice(cur);
+    }
+    delete geom;
+}
+
+}  // extern "C"

@@ -1,0 +1,174 @@
+// Internal declarations shared by the translation units of libct.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "ct.h"
+
+namespace ct {
+
+// Zero borders of the working copies the operators gather from.  With these
+// borders every bilinear neighbour of a sample that lies inside the clipped
+// plane range (projector) or the clamped row range (back-projector) is in
+// bounds, so the inner loops carry no bounds tests.
+constexpr int PAD_A = 2;   // voxels, around the in-plane and z axes of the plane-major copies
+constexpr int PAD_U = 1;   // pixels, both ends of each detector row
+constexpr int PAD_V = 2;   // rows, above and below each view
+
+// Per-view constants of the projector, from which a ray's direction, its
+// cross product with the source position and the source position follow:
+//   d = (dx0 + u dxu, dy0 + u dyu, v dzv), (S x d)_z = u crossu, S_xy = (sx, sy).
+struct ViewA {
+    float dx0, dxu, dy0, dyu, dzv, crossu, sx, sy;
+};
+
+// Per-view constants of the voxel-driven back-projector: for a voxel at
+// (x, y, z) the depth is W = w0 + x wx + y wy, the in-plane detector
+// coordinate numerator is t = x tx + y ty, the magnification M = mnum / W,
+// u = M t, v = M z and the weight kB M^2.
+struct ViewB {
+    float w0, wx, wy, tx, ty, mnum, pad0, pad1;
+};
+
+// Geometry as the kernels see it (passed by value).
+struct GeomDev {
+    int kind;
+    int nx, ny, nz, n_views, nu, nv;
+    float vox, inv_vox, du, dv, inv_du, inv_dv;
+    float cx, cy, cz, cu, cv;   // (N-1)/2 of each axis
+    float kB;                   // back-projector weight constant
+    float sdd;                  // cone: source-detector distance (cosine weight)
+    const ViewA *viewA;
+    const ViewB *viewB;
+    const float *ramp_taps;     // nu scaled Ram-Lak taps h[0..nu-1]
+    // projector working copies: plane-major, zero border PAD_A
+    //   Xc[zp][x][yp] (planes along x, rows along y), Yc[zp][y][xp]
+    int nzp;                    // nz + 2 PAD_A
+    int pitchX;                 // ny + 2 PAD_A
+    int pitchY;                 // nx + 2 PAD_A
+    // padded sinogram: S[view][vp][up], vp in [0, nv + 2 PAD_V), up in [0, nu + 2 PAD_U)
+    int nvp, pitchU;
+};
+
+// Layout of a sinogram buffer that an operator writes or reads.
+struct SinoLayout {
+    int rows_per_view;  // nv (plain) or nv + 2 PAD_V (padded)
+    int pitch;          // nu (plain) or nu + 2 PAD_U (padded)
+    int row_off;        // 0 or PAD_V
+    int col_off;        // 0 or PAD_U
+};
+
+inline SinoLayout plain_layout(const GeomDev &g) { return SinoLayout{g.nv, g.nu, 0, 0}; }
+inline SinoLayout padded_layout(const GeomDev &g) { return SinoLayout{g.nvp, g.pitchU, PAD_V, PAD_U}; }
+
+// Error reporting: thread-local message returned by ct_last_error().
+ct_status set_error(ct_status st, const char *fmt, ...);
+ct_status cuda_error(cudaError_t e, const char *what);
+
+#define CT_CUDA(call)                                                        \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return ::ct::cuda_error(e_, #call);           \
+    } while (0)
+
+#define CT_LAUNCH_CHECK(what)                                                \
+    do {                                                                     \
+        cudaError_t e_ = cudaGetLastError();                                 \
+        if (e_ != cudaSuccess) return ::ct::cuda_error(e_, what);            \
+    } while (0)
+
+// Device memory carved out of one buffer (caller workspace or one
+// stream-ordered allocation).
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0;
+    size_t used = 0;
+    bool owned = false;
+    cudaStream_t stream = nullptr;
+    static size_t align(size_t b) { return (b + 255) & ~size_t(255); }
+    template <typename T>
+    T *take(size_t count) {
+        size_t b = align(count * sizeof(T));
+        if (!base) {  // counting mode: only add up the size
+            used += b;
+            return nullptr;
+        }
+        if (used + b > size) return nullptr;
+        T *p = reinterpret_cast<T *>(base + used);
+        used += b;
+        return p;
+    }
+};
+// Opens an arena of `bytes`: uses the caller's workspace when given (and
+// large enough), else cudaMallocAsync on `stream`.
+ct_status arena_open(Arena &a, size_t bytes, void *workspace, size_t workspace_bytes,
+                     cudaStream_t stream);
+void arena_close(Arena &a);
+
+// Sizes (bytes, each rounded to 256) of the operator working buffers.
+size_t plane_copies_bytes(const GeomDev &g);      // Xc + Yc
+size_t padded_sino_bytes(const GeomDev &g);
+
+// --- projector (ct_project.cu) ---------------------------------------------------
+// Builds the plane-major zero-bordered copies Xc, Yc of the volume `vol`
+// scaled by (*scale) when scale != nullptr; when `normalize_inplace` the
+// scaled volume is also written back to `vol` (Arnoldi normalisation).
+cudaError_t launch_plane_copies(const GeomDev &g, float *vol, const double *scale,
+                                bool normalize_inplace, float *Xc, float *Yc,
+                                const int *stop, cudaStream_t st);
+// y = A x from the plane copies, written in `lay`.
+cudaError_t launch_joseph_A(const GeomDev &g, const float *Xc, const float *Yc, float *y,
+                            SinoLayout lay, const int *stop, cudaStream_t st);
+// x += A^T y (x must be zeroed by the caller); y in plain layout.
+cudaError_t launch_joseph_At(const GeomDev &g, const float *y, float *x, const int *stop,
+                             cudaStream_t st);
+
+// --- back-projector (ct_backproject.cu) ------------------------------------------
+// Copies a plain sinogram into the padded layout, scaled by (*scale) when
+// given; `normalize_inplace` also writes the scaled values back to `src`.
+cudaError_t launch_pad_sino(const GeomDev &g, float *src, const double *scale,
+                            bool normalize_inplace, float *dst, const int *stop,
+                            cudaStream_t st);
+// dst = F src (or F^T src) from a plain sinogram into layout `lay`.
+cudaError_t launch_ramp(const GeomDev &g, const float *src, float *dst, SinoLayout lay,
+                        bool transpose, const int *stop, cudaStream_t st);
+// x = B_un y from the padded sinogram.
+cudaError_t launch_voxel_B(const GeomDev &g, const float *ypad, float *x, const int *stop,
+                           cudaStream_t st);
+// y += B_un^T x (y plain, zeroed by the caller).
+cudaError_t launch_voxel_Bt(const GeomDev &g, const float *x, float *y, const int *stop,
+                            cudaStream_t st);
+
+// --- vector kernels (ct_krylov.cu) ---------------------------------------------
+int num_sms();
+
+// --- optional per-kernel timing (ct_profile.cu) ----------------------------------
+enum ProfKind {
+    PK_PLANE_COPIES = 0, PK_JOSEPH_A, PK_RAMP, PK_PAD_SINO, PK_VOXEL_B, PK_MGS, PK_SMALL,
+    PK_COMBINE, PK_JOSEPH_AT, PK_VOXEL_BT, PK_CGLS_VEC, PROF_KINDS
+};
+// Records a CUDA event pair around the launches made in its scope when
+// profiling is on (ct_profile_enable); costs one mutex lock otherwise.
+class ProfScope {
+public:
+    ProfScope(int kind, cudaStream_t st);
+    ~ProfScope();
+    ProfScope(const ProfScope &) = delete;
+    ProfScope &operator=(const ProfScope &) = delete;
+private:
+    int kind_;
+    cudaStream_t st_;
+    void *a_;
+};
+
+}  // namespace ct
+
+struct ct_geom {
+    ct_geom_desc desc;
+    int device;
+    ct::GeomDev g;
+    void *d_tables;
+    size_t n, m;
+};

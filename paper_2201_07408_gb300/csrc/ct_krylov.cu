@@ -1,0 +1,917 @@
+// Krylov solvers: BA-GMRES (Eq. 5), AB-GMRES (Eq. 4) and CGLS (Eqs. 2-3).
+//
+// Arnoldi with modified Gram-Schmidt (Sec. II): the newest Krylov vector q
+// is orthogonalised against the basis one vector at a time.  Each pass is
+// one streaming kernel that applies the previous projection
+// (q -= h_{i-1} v_{i-1}) and forms the next inner product <q, v_i> in the
+// same sweep over memory, so pass i reads q, v_{i-1}, v_i and writes q once.
+// Inner products: per-thread FP32 accumulation (plain FMA, or compensated
+// with an FMA two-product and a two-sum), warp-shuffle and block reductions
+// in FP64, and a last-block grid reduction in a fixed order (deterministic,
+// no spin-waits).  The Hessenberg column, the Givens rotations, the
+// residual estimate |g_{j+1}| and the final triangular solve run in FP64 in
+// one-thread kernels, so the whole solve is enqueued without host round
+// trips; a device status word stops the remaining kernels on a tolerance
+// stop, a lucky breakdown or a non-finite norm.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ct_internal.cuh"
+
+namespace ct {
+
+constexpr int RED_BLOCK = 256;
+
+enum : int { ST_RUN = 0, ST_TOL = 1, ST_LUCKY = 2, ST_NONFINITE = 3 };
+
+// Device-resident solver state.
+struct SolverState {
+    int status;
+    int iters;
+    unsigned counter;
+    int reorth_skip;
+    double inv_norm;    // scale that normalises the newest basis vector
+    double ref_sumsq;   // ||S v_j||^2 before orthogonalisation
+    double sumsq;       // ||q||^2 after orthogonalisation
+    double sumsq_pre2;  // ||q||^2 before the optional second sweep
+    // CGLS scalars
+    double gamma, gamma_new, delta, rr, data_rr;
+};
+
+// ---------------------------------------------------------------------------
+// accumulators
+// ---------------------------------------------------------------------------
+template <int MODE>
+struct Acc;
+
+template <>
+struct Acc<1> {  // FP32 FMA accumulation, FP64 reduction
+    float s = 0.0f;
+    __device__ __forceinline__ void add(float a, float b) { s = fmaf(a, b, s); }
+    __device__ __forceinline__ double value() const { return double(s); }
+};
+
+template <>
+struct Acc<0> {  // compensated: two-product (FMA) + two-sum in FP32
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        const float pe = fmaf(a, b, -p);
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(e, pe));
+    }
+    __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block sum of two values; result valid in thread 0.
+__device__ __forceinline__ void block_sum2(double &a, double &b)
+{
+    __shared__ double sa[RED_BLOCK / 32], sb[RED_BLOCK / 32];
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        sa[w] = a;
+        sb[w] = b;
+    }
+    __syncthreads();
+    if (w == 0) {
+        a = lane < RED_BLOCK / 32 ? sa[lane] : 0.0;
+        b = lane < RED_BLOCK / 32 ? sb[lane] : 0.0;
+        a = warp_sum(a);
+        b = warp_sum(b);
+    }
+}
+
+// Stores the block's partial sums; the last block to finish sums all
+// partials in block order and writes the outputs.
+__device__ __forceinline__ void grid_finish(double a, double b, double *partials, unsigned *counter,
+                                            double *out_a, double *out_b)
+{
+    __shared__ bool last;
+    block_sum2(a, b);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = b;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double ta = 0.0, tb = 0.0;
+    for (int i = threadIdx.x; i < int(gridDim.x); i += RED_BLOCK) {
+        ta += __ldcg(partials + 2 * i);
+        tb += __ldcg(partials + 2 * i + 1);
+    }
+    block_sum2(ta, tb);
+    if (threadIdx.x == 0) {
+        if (out_a) *out_a = ta;
+        if (out_b) *out_b = tb;
+        *counter = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One MGS pass: q -= (*hprev) vprev (if vprev), then <q, vcur> (if vcur) and
+// ||q||^2 (if out_sumsq).  Stops early on *stop, or on *skip when given.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(RED_BLOCK) mgs_pass_kernel(
+    float *__restrict__ q, const float *__restrict__ vprev, const double *__restrict__ hprev,
+    const float *__restrict__ vcur, size_t len, int vec4, double *__restrict__ partials,
+    unsigned *__restrict__ counter, double *__restrict__ out_dot, double *__restrict__ out_sumsq,
+    const int *__restrict__ stop, const int *__restrict__ skip)
+{
+    if ((stop && *stop) || (skip && *skip)) return;
+    const float h = vprev ? float(*hprev) : 0.0f;
+    Acc<MODE> dot, ss;
+    const size_t tid = blockIdx.x * size_t(RED_BLOCK) + threadIdx.x;
+    const size_t nth = size_t(gridDim.x) * RED_BLOCK;
+    size_t start = 0;
+    if (vec4) {
+        const size_t n4 = len / 4;
+        float4 *q4 = reinterpret_cast<float4 *>(q);
+        const float4 *p4 = reinterpret_cast<const float4 *>(vprev);
+        const float4 *c4 = reinterpret_cast<const float4 *>(vcur);
+        for (size_t i = tid; i < n4; i += nth) {
+            float4 a = q4[i];
+            if (vprev) {
+                const float4 p = __ldg(p4 + i);
+                a.x = fmaf(-h, p.x, a.x);
+                a.y = fmaf(-h, p.y, a.y);
+                a.z = fmaf(-h, p.z, a.z);
+                a.w = fmaf(-h, p.w, a.w);
+                q4[i] = a;
+            }
+            if (vcur) {
+                const float4 c = __ldg(c4 + i);
+                dot.add(a.x, c.x);
+                dot.add(a.y, c.y);
+                dot.add(a.z, c.z);
+                dot.add(a.w, c.w);
+            }
+            if (out_sumsq) {
+                ss.add(a.x, a.x);
+                ss.add(a.y, a.y);
+                ss.add(a.z, a.z);
+                ss.add(a.w, a.w);
+            }
+        }
+        start = n4 * 4;
+    }
+    for (size_t i = start + tid; i < len; i += nth) {
+        float a = q[i];
+        if (vprev) {
+            a = fmaf(-h, vprev[i], a);
+            q[i] = a;
+        }
+        if (vcur) dot.add(a, vcur[i]);
+        if (out_sumsq) ss.add(a, a);
+    }
+    grid_finish(dot.value(), ss.value(), partials, counter, out_dot, out_sumsq);
+}
+
+// sum (a - b)^2 -> *out (recomputed data residuals)
+__global__ void __launch_bounds__(RED_BLOCK) diff_sumsq_kernel(const float *__restrict__ a,
+                                                               const float *__restrict__ b, size_t len,
+                                                               double *__restrict__ partials,
+                                                               unsigned *__restrict__ counter,
+                                                               double *__restrict__ out,
+                                                               const int *__restrict__ stop)
+{
+    if (stop && *stop) return;
+    Acc<1> ss;
+    for (size_t i = blockIdx.x * size_t(RED_BLOCK) + threadIdx.x; i < len;
+         i += size_t(gridDim.x) * RED_BLOCK) {
+        const float d = a[i] - b[i];
+        ss.add(d, d);
+    }
+    grid_finish(0.0, ss.value(), partials, counter, nullptr, out);
+}
+
+static unsigned red_blocks(size_t len)
+{
+    size_t want = (len / 4 + RED_BLOCK - 1) / RED_BLOCK;
+    size_t cap = size_t(num_sms()) * 4;
+    return unsigned(std::max<size_t>(1, std::min(want, cap)));
+}
+
+static size_t partials_count() { return size_t(num_sms()) * 4 * 2; }
+
+static cudaError_t mgs_pass(int mode, float *q, const float *vprev, const double *hprev,
+                            const float *vcur, size_t len, double *partials, unsigned *counter,
+                            double *out_dot, double *out_sumsq, const int *stop, const int *skip,
+                            cudaStream_t st)
+{
+    const int vec4 = (len % 4 == 0) && (reinterpret_cast<uintptr_t>(q) % 16 == 0) &&
+                     (!vprev || reinterpret_cast<uintptr_t>(vprev) % 16 == 0) &&
+                     (!vcur || reinterpret_cast<uintptr_t>(vcur) % 16 == 0);
+    const unsigned blocks = red_blocks(len);
+    ProfScope prof(PK_MGS, st);
+    if (mode == 0)
+        mgs_pass_kernel<0><<<blocks, RED_BLOCK, 0, st>>>(q, vprev, hprev, vcur, len, vec4, partials,
+                                                         counter, out_dot, out_sumsq, stop, skip);
+    else
+        mgs_pass_kernel<1><<<blocks, RED_BLOCK, 0, st>>>(q, vprev, hprev, vcur, len, vec4, partials,
+                                                         counter, out_dot, out_sumsq, stop, skip);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Small FP64 kernels of the GMRES least-squares problem.
+// H, R: (k+1) x k, column-major with leading dimension k+1.
+// ---------------------------------------------------------------------------
+__global__ void gmres_init_kernel(SolverState *st, double *g, double *resid, int k)
+{
+    const double beta = sqrt(st->sumsq);
+    for (int i = 0; i <= k; ++i) {
+        g[i] = 0.0;
+        resid[i] = -1.0;
+    }
+    g[0] = beta;
+    resid[0] = beta;
+    st->iters = 0;
+    st->status = ST_RUN;
+    if (!isfinite(beta)) {
+        st->status = ST_NONFINITE;
+    } else if (beta == 0.0) {
+        st->status = ST_LUCKY;  // b (or B b) is zero: x = 0 is exact
+    } else {
+        st->inv_norm = 1.0 / beta;
+    }
+}
+
+__global__ void sqrt_inplace_kernel(double *p) { *p = sqrt(*p); }
+
+__global__ void reorth_decide_kernel(SolverState *st)
+{
+    // second sweep only when the first removed at least half of the squared
+    // norm (||q_after|| <= ||q_before|| / sqrt 2)
+    st->reorth_skip = !(st->sumsq <= 0.5 * st->ref_sumsq);
+    st->sumsq_pre2 = st->sumsq;
+}
+
+__global__ void givens_kernel(int j, int k, double *H, const double *H2, double *R, double *cs,
+                              double *sn, double *g, double *resid, SolverState *st, double tol)
+{
+    if (st->status != ST_RUN) return;
+    const int ld = k + 1;
+    double *h = H + size_t(j) * ld;
+    if (H2 && !st->reorth_skip)
+        for (int i = 0; i <= j; ++i) h[i] += H2[i];
+    const double hnext = sqrt(st->sumsq);
+    const double ref = sqrt(st->ref_sumsq);
+    h[j + 1] = hnext;
+    bool bad = !isfinite(hnext) || !isfinite(ref);
+    for (int i = 0; i <= j; ++i) bad = bad || !isfinite(h[i]);
+    if (bad) {
+        st->status = ST_NONFINITE;
+        return;
+    }
+    const bool lucky = hnext <= 1e-14 * ref;
+    double *r = R + size_t(j) * ld;
+    for (int i = 0; i <= j; ++i) r[i] = h[i];
+    r[j + 1] = lucky ? 0.0 : hnext;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * r[i] + sn[i] * r[i + 1];
+        r[i + 1] = -sn[i] * r[i] + cs[i] * r[i + 1];
+        r[i] = t;
+    }
+    const double a = r[j], b = r[j + 1];
+    const double rr = hypot(a, b);
+    double c = 1.0, s = 0.0;
+    if (rr != 0.0) {
+        c = a / rr;
+        s = b / rr;
+    }
+    cs[j] = c;
+    sn[j] = s;
+    r[j] = rr;
+    r[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    resid[j + 1] = fabs(g[j + 1]);
+    st->iters = j + 1;
+    if (lucky || rr == 0.0) {
+        st->status = ST_LUCKY;
+    } else {
+        st->inv_norm = 1.0 / hnext;
+        if (tol > 0.0 && resid[j + 1] <= tol * resid[0]) st->status = ST_TOL;
+    }
+}
+
+__global__ void backsolve_kernel(const double *R, const double *g, double *y, const SolverState *st, int k)
+{
+    const int it = st->iters;
+    const int ld = k + 1;
+    for (int i = it - 1; i >= 0; --i) {
+        double acc = g[i];
+        for (int l = i + 1; l < it; ++l) acc -= R[size_t(l) * ld + i] * y[l];
+        const double d = R[size_t(i) * ld + i];
+        y[i] = d != 0.0 ? acc / d : 0.0;
+    }
+}
+
+// x = sum_{i < count} y_i V_i ; count = *count_ptr when given, else k
+__global__ void __launch_bounds__(RED_BLOCK) combine_kernel(const float *__restrict__ V, size_t ldv, int k,
+                                                            size_t len, const double *__restrict__ y,
+                                                            const int *__restrict__ count_ptr,
+                                                            float *__restrict__ x)
+{
+    extern __shared__ float ys[];
+    const int count = count_ptr ? min(*count_ptr, k) : k;
+    for (int i = threadIdx.x; i < count; i += RED_BLOCK) ys[i] = float(y[i]);
+    __syncthreads();
+    for (size_t e = blockIdx.x * size_t(RED_BLOCK) + threadIdx.x; e < len;
+         e += size_t(gridDim.x) * RED_BLOCK) {
+        float acc = 0.0f;
+        for (int i = 0; i < count; ++i) acc = fmaf(ys[i], __ldg(V + i * ldv + e), acc);
+        x[e] = acc;
+    }
+}
+
+static cudaError_t combine(const float *V, size_t ldv, int k, size_t len, const double *y,
+                           const int *count_ptr, float *x, cudaStream_t st)
+{
+    const size_t smem = std::max<size_t>(1, size_t(k)) * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(combine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(std::min<size_t>(smem, 200 * 1024)));
+        if (e != cudaSuccess) return e;
+    }
+    const unsigned blocks = unsigned(std::max<size_t>(1, std::min((len + RED_BLOCK - 1) / RED_BLOCK,
+                                                                  size_t(num_sms()) * 8)));
+    ProfScope prof(PK_COMBINE, st);
+    combine_kernel<<<blocks, RED_BLOCK, smem, st>>>(V, ldv, k, len, y, count_ptr, x);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// CGLS vector kernels (coefficients from device scalars).
+// ---------------------------------------------------------------------------
+// y += sign * (*num / *den) * x ; optionally ||y||^2
+__global__ void __launch_bounds__(RED_BLOCK) axpy_ratio_kernel(float *__restrict__ y, const float *__restrict__ x,
+                                                               const double *__restrict__ num,
+                                                               const double *__restrict__ den, float sign,
+                                                               size_t len, double *__restrict__ partials,
+                                                               unsigned *__restrict__ counter,
+                                                               double *__restrict__ out_sumsq,
+                                                               const int *__restrict__ stop)
+{
+    if (stop && *stop) return;
+    const float a = sign * float(*num / *den);
+    Acc<1> ss;
+    for (size_t i = blockIdx.x * size_t(RED_BLOCK) + threadIdx.x; i < len;
+         i += size_t(gridDim.x) * RED_BLOCK) {
+        const float v = fmaf(a, x[i], y[i]);
+        y[i] = v;
+        ss.add(v, v);
+    }
+    if (out_sumsq) grid_finish(0.0, ss.value(), partials, counter, nullptr, out_sumsq);
+}
+
+// p = s + (*num / *den) p
+__global__ void xpby_ratio_kernel(float *__restrict__ p, const float *__restrict__ s,
+                                  const double *__restrict__ num, const double *__restrict__ den,
+                                  size_t len, const int *__restrict__ stop)
+{
+    if (stop && *stop) return;
+    const float b = float(*num / *den);
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < len;
+         i += size_t(gridDim.x) * blockDim.x)
+        p[i] = fmaf(b, p[i], s[i]);
+}
+
+__global__ void cgls_check_kernel(SolverState *st, int phase)
+{
+    if (st->status != ST_RUN) return;
+    if (phase == 0) {  // after delta = ||A p||^2
+        if (!isfinite(st->delta) || !isfinite(st->gamma)) st->status = ST_NONFINITE;
+        else if (st->delta == 0.0 || st->gamma == 0.0) st->status = ST_LUCKY;
+    }
+}
+
+__global__ void cgls_record_kernel(SolverState *st, double *resid, int j, int use_data, double tol)
+{
+    if (st->status != ST_RUN) return;
+    const double v = sqrt(use_data ? st->data_rr : st->rr);
+    resid[j] = v;
+    st->iters = j;
+    if (!isfinite(v) || !isfinite(st->gamma_new)) {
+        st->status = ST_NONFINITE;
+        return;
+    }
+    if (tol > 0.0 && v <= tol * resid[0]) st->status = ST_TOL;
+}
+
+__global__ void cgls_shift_kernel(SolverState *st)
+{
+    if (st->status != ST_RUN) return;
+    st->gamma = st->gamma_new;
+}
+
+__global__ void cgls_init_kernel(SolverState *st, double *resid, int k)
+{
+    for (int i = 0; i <= k; ++i) resid[i] = -1.0;
+    resid[0] = sqrt(st->rr);
+    st->iters = 0;
+    st->status = ST_RUN;
+    if (!isfinite(st->gamma) || !isfinite(resid[0])) st->status = ST_NONFINITE;
+    else if (st->gamma == 0.0) st->status = ST_LUCKY;
+}
+
+// ---------------------------------------------------------------------------
+// Operator plumbing shared by the solvers.
+// ---------------------------------------------------------------------------
+struct OpBufs {
+    float *Xc = nullptr, *Yc = nullptr;  // plane-major volume copies
+    float *ypad = nullptr;               // padded sinogram
+    float *t = nullptr;                  // plain sinogram
+};
+
+static void take_op_bufs(Arena &ar, const GeomDev &g, OpBufs &b, bool need_t)
+{
+    b.Xc = ar.take<float>(size_t(g.nzp) * g.nx * g.pitchX);
+    b.Yc = ar.take<float>(size_t(g.nzp) * g.ny * g.pitchY);
+    b.ypad = ar.take<float>(size_t(g.n_views) * g.nvp * g.pitchU);
+    b.t = need_t ? ar.take<float>(size_t(g.n_views) * g.nv * g.nu) : nullptr;
+}
+
+// out_vol = B sino.  `sino` is a plain sinogram, scaled by (*scale) first when
+// given (and normalised in place when `normalize`).
+static cudaError_t apply_B(const GeomDev &g, int b_kind, float *sino, const double *scale, bool normalize,
+                           OpBufs &b, float *out_vol, const int *stop, cudaStream_t st,
+                           float *scratch_vec /* n floats for A^T zeroing, unused otherwise */)
+{
+    (void)scratch_vec;
+    cudaError_t e = cudaSuccess;
+    if (b_kind == CT_B_UN) {
+        e = launch_pad_sino(g, sino, scale, normalize, b.ypad, stop, st);
+        if (e == cudaSuccess) e = launch_voxel_B(g, b.ypad, out_vol, stop, st);
+        return e;
+    }
+    if (scale) {
+        // normalise in place through the padded copy (values only), then filter / scatter
+        e = launch_pad_sino(g, sino, scale, true, b.ypad, stop, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (b_kind == CT_B_FBP) {
+        e = launch_ramp(g, sino, b.ypad, padded_layout(g), false, stop, st);
+        if (e == cudaSuccess) e = launch_voxel_B(g, b.ypad, out_vol, stop, st);
+        return e;
+    }
+    // exact transpose A^T
+    e = cudaMemsetAsync(out_vol, 0, size_t(g.nx) * g.ny * g.nz * sizeof(float), st);
+    if (e == cudaSuccess) e = launch_joseph_At(g, sino, out_vol, stop, st);
+    return e;
+}
+
+static ct_status check_common(const ct_geom *geom, const float *b, int k, const float *x,
+                              const ct_solve_opts *o)
+{
+    if (!geom || !b || !x) return set_error(CT_EINVAL, "solver: NULL argument");
+    if (k < 1) return set_error(CT_EINVAL, "solver: k must be >= 1 (got %d)", k);
+    if (k > 4096) return set_error(CT_EINVAL, "solver: k must be <= 4096 (got %d)", k);
+    if (o->b_kind != CT_B_UN && o->b_kind != CT_B_FBP && o->b_kind != CT_B_AT)
+        return set_error(CT_EINVAL, "solver: unknown b_kind %d", o->b_kind);
+    if (o->dot_mode != 0 && o->dot_mode != 1)
+        return set_error(CT_EINVAL, "solver: dot_mode must be 0 or 1");
+    if (!(o->tol >= 0.0)) return set_error(CT_EINVAL, "solver: tol must be >= 0");
+    return CT_OK;
+}
+
+static size_t round_ld(size_t len) { return (len + 63) & ~size_t(63); }
+
+// Carves the GMRES workspace; with a counting arena (base == nullptr) it
+// only adds up the size.
+struct GmresWs {
+    float *V = nullptr;
+    size_t ldv = 0;
+    OpBufs ob;
+    float *tvol = nullptr;  // AB-GMRES: B v_j
+    double *H = nullptr, *H2 = nullptr, *R = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr,
+           *resid = nullptr, *y = nullptr, *partials = nullptr;
+    SolverState *st = nullptr;
+};
+
+static bool carve_gmres(Arena &ar, const GeomDev &g, int k, bool ab, int b_kind, GmresWs &w)
+{
+    const size_t n = size_t(g.nx) * g.ny * g.nz;
+    const size_t m = size_t(g.n_views) * g.nv * g.nu;
+    const size_t len = ab ? m : n;
+    w.ldv = round_ld(len);
+    w.V = ar.take<float>(w.ldv * size_t(k + 1));
+    // BA needs a plain sinogram when B reads one (F or A^T); AB never does
+    take_op_bufs(ar, g, w.ob, !ab && b_kind != CT_B_UN);
+    if (ab) w.tvol = ar.take<float>(n);
+    const size_t ld = size_t(k) + 1;
+    w.H = ar.take<double>(ld * k);
+    w.H2 = ar.take<double>(ld);
+    w.R = ar.take<double>(ld * k);
+    w.cs = ar.take<double>(k);
+    w.sn = ar.take<double>(k);
+    w.g = ar.take<double>(ld);
+    w.resid = ar.take<double>(ld);
+    w.y = ar.take<double>(k);
+    w.partials = ar.take<double>(partials_count());
+    w.st = ar.take<SolverState>(1);
+    return w.st != nullptr;
+}
+
+static size_t gmres_bytes(const GeomDev &g, int k, bool ab, int b_kind)
+{
+    Arena ar;
+    ar.size = ~size_t(0) >> 1;
+    ar.base = nullptr;
+    GmresWs w;
+    carve_gmres(ar, g, k, ab, b_kind, w);
+    return ar.used;
+}
+
+// Enqueues the MGS sweep of iteration j (q = V_{j+1}) and its Givens step.
+static cudaError_t arnoldi_orthogonalise(GmresWs &w, int j, int k, size_t len, const ct_solve_opts &o,
+                                         cudaStream_t s)
+{
+    const int *stop = &w.st->status;
+    unsigned *ctr = &w.st->counter;
+    float *q = w.V + size_t(j + 1) * w.ldv;
+    double *hcol = w.H + size_t(j) * (k + 1);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i <= j + 1 && e == cudaSuccess; ++i) {
+        const float *vprev = i > 0 ? w.V + size_t(i - 1) * w.ldv : nullptr;
+        const double *hprev = i > 0 ? hcol + (i - 1) : nullptr;
+        const float *vcur = i <= j ? w.V + size_t(i) * w.ldv : nullptr;
+        double *odot = i <= j ? hcol + i : nullptr;
+        double *oss = i == 0 ? &w.st->ref_sumsq : (i == j + 1 ? &w.st->sumsq : nullptr);
+        e = mgs_pass(o.dot_mode, q, vprev, hprev, vcur, len, w.partials, ctr, odot, oss, stop, nullptr, s);
+    }
+    if (e != cudaSuccess) return e;
+    const double *H2 = nullptr;
+    if (o.reorth) {
+        { ProfScope prof(PK_SMALL, s); reorth_decide_kernel<<<1, 1, 0, s>>>(w.st); }
+        const int *skip = &w.st->reorth_skip;
+        for (int i = 0; i <= j + 1 && e == cudaSuccess; ++i) {
+            const float *vprev = i > 0 ? w.V + size_t(i - 1) * w.ldv : nullptr;
+            const double *hprev = i > 0 ? w.H2 + (i - 1) : nullptr;
+            const float *vcur = i <= j ? w.V + size_t(i) * w.ldv : nullptr;
+            double *odot = i <= j ? w.H2 + i : nullptr;
+            double *oss = i == j + 1 ? &w.st->sumsq : nullptr;
+            e = mgs_pass(o.dot_mode, q, vprev, hprev, vcur, len, w.partials, ctr, odot, oss, stop, skip, s);
+        }
+        if (e != cudaSuccess) return e;
+        H2 = w.H2;
+    }
+    { ProfScope prof(PK_SMALL, s); givens_kernel<<<1, 1, 0, s>>>(j, k, w.H, H2, w.R, w.cs, w.sn, w.g, w.resid, w.st, o.tol); }
+    return cudaGetLastError();
+}
+
+static ct_status finish_solve(SolverState *st_dev, const double *resid_dev, int k, double *resid_hist,
+                              int *iters_done, cudaStream_t s, const char *who)
+{
+    SolverState hst;
+    std::vector<double> hres(size_t(k) + 1);
+    CT_CUDA(cudaMemcpyAsync(&hst, st_dev, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    CT_CUDA(cudaMemcpyAsync(hres.data(), resid_dev, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, s));
+    CT_CUDA(cudaStreamSynchronize(s));
+    if (resid_hist) std::copy(hres.begin(), hres.end(), resid_hist);
+    if (iters_done) *iters_done = hst.iters;
+    if (hst.status == ST_NONFINITE)
+        return set_error(CT_ENONFINITE, "%s: a norm became NaN/Inf after %d iterations", who, hst.iters);
+    if (hst.status == ST_LUCKY) return CT_BREAKDOWN_LUCKY;
+    return CT_OK;
+}
+
+static ct_status open_ws(Arena &ar, size_t bytes, const ct_solve_opts &o, cudaStream_t s)
+{
+    return arena_open(ar, bytes, o.workspace, o.workspace_bytes, s);
+}
+
+// ---------------------------------------------------------------------------
+// BA-GMRES
+// ---------------------------------------------------------------------------
+static ct_status bagmres(const ct_geom *geom, const float *b, int k, float *x, double *resid_hist,
+                         const ct_solve_opts &o, int *iters_done, cudaStream_t s)
+{
+    const GeomDev &g = geom->g;
+    const size_t n = geom->n;
+    Arena ar;
+    ct_status rc = open_ws(ar, gmres_bytes(g, k, false, o.b_kind), o, s);
+    if (rc != CT_OK) return rc;
+    GmresWs w;
+    carve_gmres(ar, g, k, false, o.b_kind, w);
+    const int *stop = &w.st->status;
+    cudaError_t e = cudaMemsetAsync(w.st, 0, sizeof(SolverState), s);
+    // zero the padded sinogram once: its border is never written afterwards
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(w.ob.ypad, 0, size_t(g.n_views) * g.nvp * g.pitchU * sizeof(float), s);
+    // r0 = B b -> V_0
+    if (e == cudaSuccess)
+        e = apply_B(g, o.b_kind, const_cast<float *>(b), nullptr, false, w.ob, w.V, nullptr, s, nullptr);
+    if (e == cudaSuccess)
+        e = mgs_pass(o.dot_mode, w.V, nullptr, nullptr, nullptr, n, w.partials, &w.st->counter, nullptr,
+                     &w.st->sumsq, nullptr, nullptr, s);
+    if (e == cudaSuccess) {
+        { ProfScope prof(PK_SMALL, s); gmres_init_kernel<<<1, 1, 0, s>>>(w.st, w.g, w.resid, k); }
+        e = cudaGetLastError();
+    }
+    for (int j = 0; j < k && e == cudaSuccess; ++j) {
+        float *vj = w.V + size_t(j) * w.ldv;
+        // normalise v_j in place while building the projector's plane copies
+        e = launch_plane_copies(g, vj, &w.st->inv_norm, true, w.ob.Xc, w.ob.Yc, stop, s);
+        float *q = w.V + size_t(j + 1) * w.ldv;
+        if (e != cudaSuccess) break;
+        if (o.b_kind == CT_B_UN) {
+            e = launch_joseph_A(g, w.ob.Xc, w.ob.Yc, w.ob.ypad, padded_layout(g), stop, s);
+            if (e == cudaSuccess) e = launch_voxel_B(g, w.ob.ypad, q, stop, s);
+        } else {
+            e = launch_joseph_A(g, w.ob.Xc, w.ob.Yc, w.ob.t, plain_layout(g), stop, s);
+            if (e == cudaSuccess) e = apply_B(g, o.b_kind, w.ob.t, nullptr, false, w.ob, q, stop, s, nullptr);
+        }
+        if (e == cudaSuccess) e = arnoldi_orthogonalise(w, j, k, n, o, s);
+    }
+    if (e == cudaSuccess) {
+        { ProfScope prof(PK_SMALL, s); backsolve_kernel<<<1, 1, 0, s>>>(w.R, w.g, w.y, w.st, k); }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = combine(w.V, w.ldv, k, n, w.y, &w.st->iters, x, s);
+    if (e != cudaSuccess) {
+        arena_close(ar);
+        return cuda_error(e, "ct_bagmres_solve launch");
+    }
+    rc = finish_solve(w.st, w.resid, k, resid_hist, iters_done, s, "ct_bagmres_solve");
+    arena_close(ar);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// AB-GMRES
+// ---------------------------------------------------------------------------
+static ct_status abgmres(const ct_geom *geom, const float *b, int k, float *x, double *resid_hist,
+                         const ct_solve_opts &o, int *iters_done, cudaStream_t s)
+{
+    const GeomDev &g = geom->g;
+    const size_t m = geom->m;
+    Arena ar;
+    ct_status rc = open_ws(ar, gmres_bytes(g, k, true, o.b_kind), o, s);
+    if (rc != CT_OK) return rc;
+    GmresWs w;
+    carve_gmres(ar, g, k, true, o.b_kind, w);
+    const int *stop = &w.st->status;
+    cudaError_t e = cudaMemsetAsync(w.st, 0, sizeof(SolverState), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.ob.ypad, 0, size_t(g.n_views) * g.nvp * g.pitchU * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w.V, b, m * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = mgs_pass(o.dot_mode, w.V, nullptr, nullptr, nullptr, m, w.partials, &w.st->counter, nullptr,
+                     &w.st->sumsq, nullptr, nullptr, s);
+    if (e == cudaSuccess) {
+        { ProfScope prof(PK_SMALL, s); gmres_init_kernel<<<1, 1, 0, s>>>(w.st, w.g, w.resid, k); }
+        e = cudaGetLastError();
+    }
+    for (int j = 0; j < k && e == cudaSuccess; ++j) {
+        float *vj = w.V + size_t(j) * w.ldv;
+        float *q = w.V + size_t(j + 1) * w.ldv;
+        e = apply_B(g, o.b_kind, vj, &w.st->inv_norm, true, w.ob, w.tvol, stop, s, nullptr);
+        if (e == cudaSuccess) e = launch_plane_copies(g, w.tvol, nullptr, false, w.ob.Xc, w.ob.Yc, stop, s);
+        if (e == cudaSuccess) e = launch_joseph_A(g, w.ob.Xc, w.ob.Yc, q, plain_layout(g), stop, s);
+        if (e == cudaSuccess) e = arnoldi_orthogonalise(w, j, k, m, o, s);
+    }
+    if (e == cudaSuccess) {
+        { ProfScope prof(PK_SMALL, s); backsolve_kernel<<<1, 1, 0, s>>>(w.R, w.g, w.y, w.st, k); }
+        e = cudaGetLastError();
+    }
+    // u = V y (data space) into the last basis slot, then x = B u
+    float *u = w.V + size_t(k) * w.ldv;
+    if (e == cudaSuccess) e = combine(w.V, w.ldv, k, m, w.y, &w.st->iters, u, s);
+    if (e == cudaSuccess) e = apply_B(g, o.b_kind, u, nullptr, false, w.ob, x, nullptr, s, nullptr);
+    if (e != cudaSuccess) {
+        arena_close(ar);
+        return cuda_error(e, "ct_abgmres_solve launch");
+    }
+    rc = finish_solve(w.st, w.resid, k, resid_hist, iters_done, s, "ct_abgmres_solve");
+    arena_close(ar);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// CGLS with back-projector B
+// ---------------------------------------------------------------------------
+struct CglsWs {
+    OpBufs ob;
+    float *r = nullptr, *s = nullptr, *p = nullptr, *q = nullptr, *ax = nullptr;
+    double *resid = nullptr, *partials = nullptr;
+    SolverState *st = nullptr;
+};
+
+static void carve_cgls(Arena &ar, const GeomDev &g, int k, bool data_resid, CglsWs &w)
+{
+    const size_t n = size_t(g.nx) * g.ny * g.nz;
+    const size_t m = size_t(g.n_views) * g.nv * g.nu;
+    take_op_bufs(ar, g, w.ob, false);
+    w.r = ar.take<float>(m);
+    w.q = ar.take<float>(m);
+    w.s = ar.take<float>(n);
+    w.p = ar.take<float>(n);
+    w.ax = data_resid ? ar.take<float>(m) : nullptr;
+    w.resid = ar.take<double>(size_t(k) + 1);
+    w.partials = ar.take<double>(partials_count());
+    w.st = ar.take<SolverState>(1);
+}
+
+static size_t cgls_ws_bytes(const GeomDev &g, int k, bool data_resid)
+{
+    Arena ar;
+    ar.size = ~size_t(0) >> 1;
+    CglsWs w;
+    carve_cgls(ar, g, k, data_resid, w);
+    return ar.used;
+}
+
+static ct_status cgls(const ct_geom *geom, const float *b, int k, float *x, double *resid_hist,
+                      const ct_solve_opts &o, int *iters_done, cudaStream_t s)
+{
+    const GeomDev &g = geom->g;
+    const size_t n = geom->n, m = geom->m;
+    const bool data = o.record_data_resid != 0;
+    Arena ar;
+    ct_status rc = open_ws(ar, cgls_ws_bytes(g, k, data), o, s);
+    if (rc != CT_OK) return rc;
+    CglsWs w;
+    carve_cgls(ar, g, k, data, w);
+    SolverState *st = w.st;
+    const int *stop = &st->status;
+    unsigned *ctr = &st->counter;
+    const unsigned vb = red_blocks(std::max(n, m));
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(SolverState), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.ob.ypad, 0, size_t(g.n_views) * g.nvp * g.pitchU * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, n * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w.r, b, m * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    // rr = ||r||^2, s = B r, gamma = ||s||^2, p = s
+    if (e == cudaSuccess)
+        e = mgs_pass(1, w.r, nullptr, nullptr, nullptr, m, w.partials, ctr, nullptr, &st->rr, nullptr, nullptr, s);
+    if (e == cudaSuccess) e = apply_B(g, o.b_kind, w.r, nullptr, false, w.ob, w.s, nullptr, s, nullptr);
+    if (e == cudaSuccess)
+        e = mgs_pass(1, w.s, nullptr, nullptr, nullptr, n, w.partials, ctr, nullptr, &st->gamma, nullptr, nullptr, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w.p, w.s, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) {
+        { ProfScope prof(PK_SMALL, s); cgls_init_kernel<<<1, 1, 0, s>>>(st, w.resid, k); }
+        e = cudaGetLastError();
+    }
+    for (int j = 1; j <= k && e == cudaSuccess; ++j) {
+        // q = A p ; delta = ||q||^2
+        e = launch_plane_copies(g, w.p, nullptr, false, w.ob.Xc, w.ob.Yc, stop, s);
+        if (e == cudaSuccess) e = launch_joseph_A(g, w.ob.Xc, w.ob.Yc, w.q, plain_layout(g), stop, s);
+        if (e == cudaSuccess)
+            e = mgs_pass(1, w.q, nullptr, nullptr, nullptr, m, w.partials, ctr, nullptr, &st->delta, stop, nullptr, s);
+        if (e == cudaSuccess) {
+            { ProfScope prof(PK_SMALL, s); cgls_check_kernel<<<1, 1, 0, s>>>(st, 0); }
+            e = cudaGetLastError();
+        }
+        // x += alpha p ; r -= alpha q (alpha = gamma / delta) ; rr = ||r||^2
+        if (e == cudaSuccess) {
+            ProfScope prof(PK_CGLS_VEC, s);
+            axpy_ratio_kernel<<<vb, RED_BLOCK, 0, s>>>(x, w.p, &st->gamma, &st->delta, 1.0f, n, w.partials,
+                                                       ctr, nullptr, stop);
+            axpy_ratio_kernel<<<vb, RED_BLOCK, 0, s>>>(w.r, w.q, &st->gamma, &st->delta, -1.0f, m, w.partials,
+                                                       ctr, &st->rr, stop);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess && data) {
+            e = launch_plane_copies(g, x, nullptr, false, w.ob.Xc, w.ob.Yc, stop, s);
+            if (e == cudaSuccess) e = launch_joseph_A(g, w.ob.Xc, w.ob.Yc, w.ax, plain_layout(g), stop, s);
+            if (e == cudaSuccess) {
+                { ProfScope prof(PK_CGLS_VEC, s); diff_sumsq_kernel<<<vb, RED_BLOCK, 0, s>>>(b, w.ax, m, w.partials, ctr, &st->data_rr, stop); }
+                e = cudaGetLastError();
+            }
+        }
+        // s = B r ; gamma_new = ||s||^2 ; p = s + (gamma_new/gamma) p ; gamma = gamma_new
+        if (e == cudaSuccess) e = apply_B(g, o.b_kind, w.r, nullptr, false, w.ob, w.s, stop, s, nullptr);
+        if (e == cudaSuccess)
+            e = mgs_pass(1, w.s, nullptr, nullptr, nullptr, n, w.partials, ctr, nullptr, &st->gamma_new, stop,
+                         nullptr, s);
+        if (e == cudaSuccess) {
+            { ProfScope prof(PK_SMALL, s); cgls_record_kernel<<<1, 1, 0, s>>>(st, w.resid, j, data ? 1 : 0, o.tol); }
+            { ProfScope prof(PK_CGLS_VEC, s); xpby_ratio_kernel<<<vb, RED_BLOCK, 0, s>>>(w.p, w.s, &st->gamma_new, &st->gamma, n, stop); }
+            { ProfScope prof(PK_SMALL, s); cgls_shift_kernel<<<1, 1, 0, s>>>(st); }
+            e = cudaGetLastError();
+        }
+    }
+    if (e != cudaSuccess) {
+        arena_close(ar);
+        return cuda_error(e, "ct_cgls_solve launch");
+    }
+    rc = finish_solve(st, w.resid, k, resid_hist, iters_done, s, "ct_cgls_solve");
+    arena_close(ar);
+    return rc;
+}
+
+}  // namespace ct
+
+using namespace ct;
+
+static ct_solve_opts resolve_opts(const ct_solve_opts *opts)
+{
+    ct_solve_opts o;
+    ct_solve_opts_default(&o);
+    if (opts) o = *opts;
+    return o;
+}
+
+extern "C" {
+
+size_t ct_workspace_bytes(const ct_geom *geom, int k, int solver, const ct_solve_opts *opts)
+{
+    if (!geom || k < 1) return 0;
+    ct_solve_opts o = resolve_opts(opts);
+    switch (solver) {
+    case CT_SOLVER_BA: return gmres_bytes(geom->g, k, false, o.b_kind);
+    case CT_SOLVER_AB: return gmres_bytes(geom->g, k, true, o.b_kind);
+    case CT_SOLVER_CGLS: return cgls_ws_bytes(geom->g, k, o.record_data_resid != 0);
+    default: return 0;
+    }
+}
+
+ct_status ct_bagmres_solve(const ct_geom *geom, const float *b_dev, int k, float *x_out_dev,
+                           double *resid_hist, const ct_solve_opts *opts, int *iters_done, void *stream)
+{
+    ct_solve_opts o = resolve_opts(opts);
+    ct_status rc = check_common(geom, b_dev, k, x_out_dev, &o);
+    if (rc != CT_OK) return rc;
+    return bagmres(geom, b_dev, k, x_out_dev, resid_hist, o, iters_done, static_cast<cudaStream_t>(stream));
+}
+
+ct_status ct_abgmres_solve(const ct_geom *geom, const float *b_dev, int k, float *x_out_dev,
+                           double *resid_hist, const ct_solve_opts *opts, int *iters_done, void *stream)
+{
+    ct_solve_opts o = resolve_opts(opts);
+    ct_status rc = check_common(geom, b_dev, k, x_out_dev, &o);
+    if (rc != CT_OK) return rc;
+    return abgmres(geom, b_dev, k, x_out_dev, resid_hist, o, iters_done, static_cast<cudaStream_t>(stream));
+}
+
+ct_status ct_cgls_solve(const ct_geom *geom, const float *b_dev, int k, float *x_out_dev,
+                        double *resid_hist, const ct_solve_opts *opts, int *iters_done, void *stream)
+{
+    ct_solve_opts o = resolve_opts(opts);
+    ct_status rc = check_common(geom, b_dev, k, x_out_dev, &o);
+    if (rc != CT_OK) return rc;
+    return cgls(geom, b_dev, k, x_out_dev, resid_hist, o, iters_done, static_cast<cudaStream_t>(stream));
+}
+
+ct_status ct_mgs_sweep(const float *V_dev, size_t ldv, int j, size_t len, float *q_dev, double *h_dev,
+                       int dot_mode, void *stream)
+{
+    if (!q_dev || !h_dev || (j > 0 && !V_dev)) return set_error(CT_EINVAL, "ct_mgs_sweep: NULL argument");
+    if (j < 0 || len == 0 || (j > 0 && ldv < len))
+        return set_error(CT_EINVAL, "ct_mgs_sweep: bad sizes (j=%d len=%zu ldv=%zu)", j, len, ldv);
+    if (dot_mode != 0 && dot_mode != 1) return set_error(CT_EINVAL, "ct_mgs_sweep: dot_mode must be 0 or 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Arena ar;
+    const size_t bytes = Arena::align(partials_count() * sizeof(double)) + Arena::align(sizeof(unsigned));
+    ct_status rc = arena_open(ar, bytes, nullptr, 0, s);
+    if (rc != CT_OK) return rc;
+    double *partials = ar.take<double>(partials_count());
+    unsigned *ctr = ar.take<unsigned>(1);
+    cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(unsigned), s);
+    for (int i = 0; i <= j && e == cudaSuccess; ++i) {
+        const float *vprev = i > 0 ? V_dev + size_t(i - 1) * ldv : nullptr;
+        const double *hprev = i > 0 ? h_dev + (i - 1) : nullptr;
+        const float *vcur = i < j ? V_dev + size_t(i) * ldv : nullptr;
+        double *odot = i < j ? h_dev + i : nullptr;
+        double *oss = i == j ? h_dev + j : nullptr;
+        e = mgs_pass(dot_mode, q_dev, vprev, hprev, vcur, len, partials, ctr, odot, oss, nullptr, nullptr, s);
+    }
+    // h[j] = sqrt(||q||^2)
+    if (e == cudaSuccess) {
+        { ProfScope prof(PK_SMALL, s); sqrt_inplace_kernel<<<1, 1, 0, s>>>(h_dev + j); }
+        e = cudaGetLastError();
+    }
+    arena_close(ar);
+    if (e != cudaSuccess) return cuda_error(e, "ct_mgs_sweep launch");
+    return CT_OK;
+}
+
+ct_status ct_basis_combine(const float *V_dev, size_t ldv, int k, size_t len, const double *y_dev,
+                           float *x_dev, void *stream)
+{
+    if (!V_dev || !y_dev || !x_dev) return set_error(CT_EINVAL, "ct_basis_combine: NULL argument");
+    if (k < 1 || len == 0 || ldv < len) return set_error(CT_EINVAL, "ct_basis_combine: bad sizes");
+    if (k > 4096) return set_error(CT_EINVAL, "ct_basis_combine: k must be <= 4096");
+    cudaError_t e = combine(V_dev, ldv, k, len, y_dev, nullptr, x_dev, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_error(e, "ct_basis_combine launch");
+    return CT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,290 @@
+// Ray-driven Joseph projector A and its exact transpose A^T.
+//
+// A (Sec. I Eq. 1, Sec. III): every detector ray walks the voxel-centre
+// planes of its dominant axis (x when |d_x| >= |d_y|, else y); on each plane
+// it takes the bilinear interpolation of the four neighbouring voxels in
+// that plane (neighbours outside the grid are zero), and the sum is scaled
+// by the step length vox |d| / |d_a|.
+//
+// GPU layout.  The gathers run against two plane-major copies of the volume
+// with a zero border of PAD_A voxels around the in-plane and z axes:
+//   Xc[zp][x][yp]  for x-dominant rays (planes along x, in-plane axis y fastest),
+//   Yc[zp][y][xp]  for y-dominant rays (planes along y, in-plane axis x fastest).
+// Neighbouring rays of a detector row then read neighbouring words, and each
+// ray's plane range is clipped up front so that the unrolled inner loop has no
+// bounds tests.  Building the copies reads the volume once and is also where
+// the Arnoldi step normalises its newest basis vector.
+//
+// Ray coordinates.  The sample position on plane p is affine in p:
+//   f_b(p) = fbc + (p - c_a) gb,  f_z(p) = fzc + (p - c_a) gz
+// with the value at the central plane computed from the cross product
+// (S x d)_z rather than from S + t d, which in FP32 would cancel two terms of
+// the size of the source distance; (S x d)_z = sod*u exactly for this
+// geometry, so the intercept keeps full relative precision.
+#include "ct_internal.cuh"
+
+namespace ct {
+
+struct RaySetup {
+    int xdom;      // 1: planes along x
+    int p0, p1;    // inclusive plane range that can hold nonzero samples
+    float ca;      // (N_a - 1)/2
+    float fbc, gb; // in-plane fractional index at the central plane, slope per plane
+    float fzc, gz; // z fractional index at the central plane, slope per plane
+    float weight;  // vox |d| / |d_a|
+};
+
+// Narrows [p0, p1] to the planes whose f(p) = fc + (p - ca) g lies in
+// [lo - 0.5, hi + 0.5].  Every sample with f in [lo, hi) stays inside; every
+// kept sample has floor(f) in [lo - 1, hi], inside the zero border.
+__device__ __forceinline__ void clip_planes(float fc, float g, float lo, float hi, float ca, int Na,
+                                            int &p0, int &p1)
+{
+    if (fabsf(g) < 1e-20f) {
+        if (!(fc >= lo - 0.5f && fc <= hi + 0.5f)) p1 = -1;
+        return;
+    }
+    float ig = 1.0f / g;
+    float t1 = (lo - 0.5f - fc) * ig + ca;
+    float t2 = (hi + 0.5f - fc) * ig + ca;
+    float tl = fmaxf(fminf(t1, t2), -1.0f);
+    float th = fminf(fmaxf(t1, t2), float(Na));
+    p0 = max(p0, int(ceilf(tl)));
+    p1 = min(p1, int(floorf(th)));
+}
+
+__device__ __forceinline__ RaySetup ray_setup(const GeomDev &g, int s, int iv, int iu)
+{
+    const float4 *vp = reinterpret_cast<const float4 *>(g.viewA + s);
+    const float4 a = __ldg(vp), b = __ldg(vp + 1);
+    // a = (dx0, dxu, dy0, dyu), b = (dzv, crossu, sx, sy)
+    const float u = (float(iu) - g.cu) * g.du;
+    const float v = (float(iv) - g.cv) * g.dv;
+    const float dx = fmaf(u, a.y, a.x);
+    const float dy = fmaf(u, a.w, a.z);
+    const float dz = v * b.x;
+    const float cross = u * b.y;
+    RaySetup r;
+    r.xdom = fabsf(dx) >= fabsf(dy);
+    const float da = r.xdom ? dx : dy;
+    const float db = r.xdom ? dy : dx;
+    const float Sa = r.xdom ? b.z : b.w;
+    const int Na = r.xdom ? g.nx : g.ny;
+    const int Nb = r.xdom ? g.ny : g.nx;
+    const float cb = r.xdom ? g.cy : g.cx;
+    r.ca = r.xdom ? g.cx : g.cy;
+    const float inv_da = 1.0f / da;
+    r.gb = db * inv_da;
+    // x-dominant: y(c) = (c d_y - cross)/d_x ; y-dominant: x(c) = (c d_x + cross)/d_y
+    const float cterm = cross * inv_da * g.inv_vox;
+    r.fbc = r.xdom ? cb - cterm : cb + cterm;
+    r.gz = dz * inv_da;
+    r.fzc = fmaf(-Sa * g.inv_vox, r.gz, g.cz);
+    r.weight = g.vox * sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * fabsf(inv_da);
+    r.p0 = 0;
+    r.p1 = Na - 1;
+    clip_planes(r.fbc, r.gb, -1.0f, float(Nb), r.ca, Na, r.p0, r.p1);
+    clip_planes(r.fzc, r.gz, -1.0f, float(g.nz), r.ca, Na, r.p0, r.p1);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Plane-major zero-bordered copies.  One block handles a 32x32 (x, y) tile
+// of one padded z slice; Yc rows are written straight from the tile, Xc rows
+// from its transpose in shared memory.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) plane_copies_kernel(GeomDev g, float *__restrict__ vol,
+                                                           const double *__restrict__ scale,
+                                                           int normalize_inplace,
+                                                           float *__restrict__ Xc,
+                                                           float *__restrict__ Yc,
+                                                           const int *__restrict__ stop)
+{
+    if (stop && *stop) return;
+    __shared__ float tile[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    const int xp0 = blockIdx.x * 32, yp0 = blockIdx.y * 32;  // padded tile origin
+    const int zp = blockIdx.z;
+    const int z = zp - PAD_A;
+    const float sc = scale ? float(*scale) : 1.0f;
+    const bool zin = z >= 0 && z < g.nz;
+    for (int r = ty; r < 32; r += 8) {
+        const int x = xp0 + tx - PAD_A, y = yp0 + r - PAD_A;
+        float val = 0.0f;
+        if (zin && x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
+            const size_t idx = (size_t(z) * g.ny + y) * g.nx + x;
+            val = vol[idx] * sc;
+            if (normalize_inplace) vol[idx] = val;
+        }
+        tile[r][tx] = val;
+    }
+    __syncthreads();
+    // Yc[zp][y][xp] for y in the grid, xp over the padded row
+    for (int r = ty; r < 32; r += 8) {
+        const int y = yp0 + r - PAD_A, xp = xp0 + tx;
+        if (y >= 0 && y < g.ny && xp < g.pitchY)
+            Yc[(size_t(zp) * g.ny + y) * g.pitchY + xp] = tile[r][tx];
+    }
+    // Xc[zp][x][yp] for x in the grid, yp over the padded row
+    for (int r = ty; r < 32; r += 8) {
+        const int x = xp0 + r - PAD_A, yp = yp0 + tx;
+        if (x >= 0 && x < g.nx && yp < g.pitchX)
+            Xc[(size_t(zp) * g.nx + x) * g.pitchX + yp] = tile[tx][r];
+    }
+}
+
+cudaError_t launch_plane_copies(const GeomDev &g, float *vol, const double *scale,
+                                bool normalize_inplace, float *Xc, float *Yc, const int *stop,
+                                cudaStream_t st)
+{
+    ProfScope prof(PK_PLANE_COPIES, st);
+    dim3 block(32, 8);
+    dim3 grid((g.nx + 2 * PAD_A + 31) / 32, (g.ny + 2 * PAD_A + 31) / 32, g.nzp);
+    plane_copies_kernel<<<grid, block, 0, st>>>(g, vol, scale, normalize_inplace ? 1 : 0, Xc, Yc,
+                                                stop);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// y = A x.  One thread per ray, rays of a detector row on neighbouring lanes.
+// ---------------------------------------------------------------------------
+constexpr int A_BLOCK = 128;
+
+__global__ void __launch_bounds__(A_BLOCK) joseph_A_kernel(GeomDev g, const float *__restrict__ Xc,
+                                                           const float *__restrict__ Yc,
+                                                           float *__restrict__ y, SinoLayout lay,
+                                                           const int *__restrict__ stop)
+{
+    if (stop && *stop) return;
+    const int ray = blockIdx.x * A_BLOCK + threadIdx.x;
+    const int per_view = g.nu * g.nv;
+    if (ray >= per_view * g.n_views) return;
+    const int s = ray / per_view;
+    const int rem = ray - s * per_view;
+    const int iv = rem / g.nu;
+    const int iu = rem - iv * g.nu;
+    const RaySetup r = ray_setup(g, s, iv, iu);
+
+    const float *__restrict__ base = r.xdom ? Xc : Yc;
+    const int Na = r.xdom ? g.nx : g.ny;
+    const int pitch = r.xdom ? g.pitchX : g.pitchY;
+    const int zstride = Na * pitch;            // one padded z slice
+    // element offset of (zp = PAD_A + z0, plane p, bp = PAD_A + b0) = (z0*Na + p)*pitch + b0 + off0
+    const int off0 = (PAD_A * Na) * pitch + PAD_A;
+
+    float acc = 0.0f;
+#pragma unroll 4
+    for (int p = r.p0; p <= r.p1; ++p) {
+        const float pm = float(p) - r.ca;
+        const float fb = fmaf(pm, r.gb, r.fbc);
+        const float fz = fmaf(pm, r.gz, r.fzc);
+        const float b0f = floorf(fb), z0f = floorf(fz);
+        const float wb = fb - b0f, wz = fz - z0f;
+        const int idx = (int(z0f) * Na + p) * pitch + int(b0f) + off0;
+        const float v00 = __ldg(base + idx);
+        const float v01 = __ldg(base + idx + 1);
+        const float v10 = __ldg(base + idx + zstride);
+        const float v11 = __ldg(base + idx + zstride + 1);
+        const float s0 = fmaf(wb, v01 - v00, v00);
+        const float s1 = fmaf(wb, v11 - v10, v10);
+        acc += fmaf(wz, s1 - s0, s0);
+    }
+    y[(size_t(s) * lay.rows_per_view + iv + lay.row_off) * lay.pitch + iu + lay.col_off] =
+        acc * r.weight;
+}
+
+cudaError_t launch_joseph_A(const GeomDev &g, const float *Xc, const float *Yc, float *y,
+                            SinoLayout lay, const int *stop, cudaStream_t st)
+{
+    const long long m = (long long)g.nu * g.nv * g.n_views;
+    const unsigned blocks = unsigned((m + A_BLOCK - 1) / A_BLOCK);
+    ProfScope prof(PK_JOSEPH_A, st);
+    joseph_A_kernel<<<blocks, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// x += A^T y: the same ray walk, scattering the four bilinear weights of
+// every sample with FP32 atomics (grid-bounded, no padding needed).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void scatter_add(float *x, const GeomDev &g, int xdom, int p, int b,
+                                            int z, float val)
+{
+    const int Nb = xdom ? g.ny : g.nx;
+    if (b < 0 || b >= Nb || z < 0 || z >= g.nz || val == 0.0f) return;
+    const int ix = xdom ? p : b;
+    const int iy = xdom ? b : p;
+    atomicAdd(x + (size_t(z) * g.ny + iy) * g.nx + ix, val);
+}
+
+__global__ void __launch_bounds__(A_BLOCK) joseph_At_kernel(GeomDev g, const float *__restrict__ y,
+                                                            float *__restrict__ x,
+                                                            const int *__restrict__ stop)
+{
+    if (stop && *stop) return;
+    const int ray = blockIdx.x * A_BLOCK + threadIdx.x;
+    const int per_view = g.nu * g.nv;
+    if (ray >= per_view * g.n_views) return;
+    const float yr = y[ray];
+    if (yr == 0.0f) return;
+    const int s = ray / per_view;
+    const int rem = ray - s * per_view;
+    const int iv = rem / g.nu;
+    const int iu = rem - iv * g.nu;
+    const RaySetup r = ray_setup(g, s, iv, iu);
+    const float val = yr * r.weight;
+    for (int p = r.p0; p <= r.p1; ++p) {
+        const float pm = float(p) - r.ca;
+        const float fb = fmaf(pm, r.gb, r.fbc);
+        const float fz = fmaf(pm, r.gz, r.fzc);
+        const float b0f = floorf(fb), z0f = floorf(fz);
+        const float wb = fb - b0f, wz = fz - z0f;
+        const int b0 = int(b0f), z0 = int(z0f);
+        scatter_add(x, g, r.xdom, p, b0, z0, val * (1.0f - wb) * (1.0f - wz));
+        scatter_add(x, g, r.xdom, p, b0 + 1, z0, val * wb * (1.0f - wz));
+        scatter_add(x, g, r.xdom, p, b0, z0 + 1, val * (1.0f - wb) * wz);
+        scatter_add(x, g, r.xdom, p, b0 + 1, z0 + 1, val * wb * wz);
+    }
+}
+
+cudaError_t launch_joseph_At(const GeomDev &g, const float *y, float *x, const int *stop,
+                             cudaStream_t st)
+{
+    const long long m = (long long)g.nu * g.nv * g.n_views;
+    const unsigned blocks = unsigned((m + A_BLOCK - 1) / A_BLOCK);
+    ProfScope prof(PK_JOSEPH_AT, st);
+    joseph_At_kernel<<<blocks, A_BLOCK, 0, st>>>(g, y, x, stop);
+    return cudaGetLastError();
+}
+
+}  // namespace ct
+
+using namespace ct;
+
+extern "C" ct_status ct_project_A(const ct_geom *geom, const float *x_dev, float *y_dev, void *stream)
+{
+    if (!geom || !x_dev || !y_dev) return set_error(CT_EINVAL, "ct_project_A: NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const GeomDev &g = geom->g;
+    Arena ar;
+    ct_status rc = arena_open(ar, plane_copies_bytes(g), nullptr, 0, st);
+    if (rc != CT_OK) return rc;
+    float *Xc = ar.take<float>(size_t(g.nzp) * g.nx * g.pitchX);
+    float *Yc = ar.take<float>(size_t(g.nzp) * g.ny * g.pitchY);
+    cudaError_t e = launch_plane_copies(g, const_cast<float *>(x_dev), nullptr, false, Xc, Yc,
+                                        nullptr, st);
+    if (e == cudaSuccess) e = launch_joseph_A(g, Xc, Yc, y_dev, plain_layout(g), nullptr, st);
+    arena_close(ar);
+    if (e != cudaSuccess) return cuda_error(e, "ct_project_A launch");
+    return CT_OK;
+}
+
+extern "C" ct_status ct_adjoint_At(const ct_geom *geom, const float *y_dev, float *x_dev, void *stream)
+{
+    if (!geom || !y_dev || !x_dev) return set_error(CT_EINVAL, "ct_adjoint_At: NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CT_CUDA(cudaMemsetAsync(x_dev, 0, geom->n * sizeof(float), st));
+    cudaError_t e = launch_joseph_At(geom->g, y_dev, x_dev, nullptr, st);
+    if (e != cudaSuccess) return cuda_error(e, "ct_adjoint_At launch");
+    return CT_OK;
+}

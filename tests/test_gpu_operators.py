@@ -1,0 +1,203 @@
+"""GPU parity of the operators A, B_un, B_FBP, F, A^T, B^T against the FP64
+oracle, through the C-ABI.
+
+Tolerance: relative L2 error <= 1e-5 per operator application (FP32
+arithmetic against FP64); the bound is stated in each assertion.  Small
+cases are compared element by element over the whole output; the 256^3 and
+512^3 scans on sampled rays / voxels that the oracle evaluates one by one.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import ct_inputs as ci
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+OP_TOL = 1e-5
+
+SMALL = [ci.CONE_SMALL, ci.CONE_ANISO, ci.PAR2D_ANISO, ci.PAR2D_64, ci.CONE_GRAD32, ci.CONE_512_CUT64]
+
+
+@pytest.fixture(scope="module")
+def ct():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2201_07408_gb300 import ct as _ct
+    return _ct
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().double().numpy()
+
+
+def volume_input(spec, kind):
+    if kind == "phantom":
+        return ci.phantom(spec)[0]
+    return ci.random_vector(spec.n, seed=61, positive=True).astype(np.float32).reshape(spec.vol_shape)
+
+
+@pytest.mark.parametrize("spec", SMALL, ids=lambda s: s.name)
+@pytest.mark.parametrize("kind", ["phantom", "random"])
+def test_project_A_matches_oracle(ct, spec, kind):
+    g = ct.Geometry.from_spec(spec)
+    x = volume_input(spec, kind)
+    y = host(ct.project_A(g, dev(x)))
+    ref = oracle.project_A(spec, x.astype(np.float64))
+    assert rel(y, ref) <= OP_TOL, rel(y, ref)
+    assert np.max(np.abs(y - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("spec", SMALL, ids=lambda s: s.name)
+@pytest.mark.parametrize("b_kind", ["un", "fbp"])
+def test_backproject_B_matches_oracle(ct, spec, b_kind):
+    g = ct.Geometry.from_spec(spec)
+    y = oracle.project_A(spec, ci.phantom(spec)[0].astype(np.float64)).astype(np.float32)
+    y = y + ci.gaussian_noise(y.shape, 0.01 * y.max(), seed=62, dtype=np.float32)
+    x = host(ct.backproject_B(g, dev(y), b_kind))
+    ref = oracle.backproject_B(spec, y.astype(np.float64), filtered=b_kind == "fbp")
+    assert rel(x, ref) <= OP_TOL, rel(x, ref)
+
+
+@pytest.mark.parametrize("spec", SMALL, ids=lambda s: s.name)
+@pytest.mark.parametrize("transpose", [False, True])
+def test_ramp_F_matches_oracle(ct, spec, transpose):
+    g = ct.Geometry.from_spec(spec)
+    y = ci.random_vector(spec.m, seed=63).astype(np.float32).reshape(spec.sino_shape)
+    out = host(ct.ramp_F(g, dev(y), transpose))
+    ref = (oracle.ramp_Ft if transpose else oracle.ramp_F)(spec, y.astype(np.float64))
+    assert rel(out, ref) <= OP_TOL, rel(out, ref)
+
+
+@pytest.mark.parametrize("spec", SMALL, ids=lambda s: s.name)
+def test_adjoint_At_matches_oracle(ct, spec):
+    g = ct.Geometry.from_spec(spec)
+    y = ci.random_vector(spec.m, seed=64).astype(np.float32).reshape(spec.sino_shape)
+    x = host(ct.adjoint_At(g, dev(y)))
+    ref = oracle.adjoint_At(spec, y.astype(np.float64))
+    assert rel(x, ref) <= OP_TOL, rel(x, ref)
+
+
+@pytest.mark.parametrize("spec", SMALL, ids=lambda s: s.name)
+@pytest.mark.parametrize("b_kind", ["un", "fbp"])
+def test_adjoint_Bt_matches_oracle(ct, spec, b_kind):
+    g = ct.Geometry.from_spec(spec)
+    x = ci.random_vector(spec.n, seed=65).astype(np.float32).reshape(spec.vol_shape)
+    y = host(ct.adjoint_Bt(g, dev(x), b_kind))
+    ref = oracle.adjoint_Bt(spec, x.astype(np.float64), filtered=b_kind == "fbp")
+    assert rel(y, ref) <= OP_TOL, rel(y, ref)
+
+
+@pytest.mark.parametrize("spec", [ci.CONE_SMALL, ci.PAR2D_ANISO], ids=lambda s: s.name)
+def test_gpu_adjoint_dot_products(ct, spec):
+    """<A x, y> = <x, A^T y> and <B y, x> = <y, B^T x> for the GPU kernels
+    themselves (FP32: ~1e-6)."""
+    g = ct.Geometry.from_spec(spec)
+    x = dev(ci.random_vector(spec.n, seed=66).reshape(spec.vol_shape))
+    y = dev(ci.random_vector(spec.m, seed=67).reshape(spec.sino_shape))
+    ax_y = float((ct.project_A(g, x).double() * y.double()).sum())
+    x_aty = float((x.double() * ct.adjoint_At(g, y).double()).sum())
+    assert abs(ax_y - x_aty) <= 1e-5 * abs(ax_y)
+    for kind in ("un", "fbp"):
+        by_x = float((ct.backproject_B(g, y, kind).double() * x.double()).sum())
+        y_btx = float((y.double() * ct.adjoint_Bt(g, x, kind).double()).sum())
+        assert abs(by_x - y_btx) <= 1e-5 * abs(by_x), kind
+
+
+def test_zero_inputs_give_exact_zeros(ct):
+    spec = ci.CONE_ANISO
+    g = ct.Geometry.from_spec(spec)
+    assert torch.count_nonzero(ct.project_A(g, torch.zeros(spec.vol_shape, device="cuda"))) == 0
+    assert torch.count_nonzero(ct.backproject_B(g, torch.zeros(spec.sino_shape, device="cuda"), "fbp")) == 0
+
+
+def test_single_voxel_and_single_ray(ct):
+    """A delta volume projects to the oracle's column of A; a delta sinogram
+    back-projects to the oracle's column of B (sparse structure, exact zeros
+    outside the footprint)."""
+    spec = ci.CONE_ANISO
+    g = ct.Geometry.from_spec(spec)
+    j = (spec.nz // 2 * spec.ny + 7) * spec.nx + 31
+    e = np.zeros(spec.n, dtype=np.float32)
+    e[j] = 1.0
+    col = host(ct.project_A(g, dev(e.reshape(spec.vol_shape)))).reshape(-1)
+    ref = oracle.project_A(spec, e.astype(np.float64)).reshape(-1)
+    assert np.array_equal(col != 0, ref != 0)
+    assert rel(col, ref) <= OP_TOL
+    r = (spec.n_views // 3 * spec.nv + spec.nv // 2) * spec.nu + 17
+    d = np.zeros(spec.m, dtype=np.float32)
+    d[r] = 1.0
+    colb = host(ct.backproject_B(g, dev(d.reshape(spec.sino_shape)))).reshape(-1)
+    refb = oracle.backproject_B(spec, d.astype(np.float64)).reshape(-1)
+    assert np.array_equal(colb != 0, refb != 0)
+    assert rel(colb, refb) <= OP_TOL
+
+
+@pytest.mark.parametrize("spec", [ci.CONE_128, ci.CONE_256], ids=lambda s: s.name)
+def test_full_size_operators_on_sampled_outputs(ct, spec):
+    """The operators at the full 128^3 / 256^3 scans, checked on seeded
+    samples of rays and voxels that the oracle evaluates one by one."""
+    g = ct.Geometry.from_spec(spec)
+    x = ci.phantom(spec)[0]
+    y = ct.project_A(g, dev(x))
+    rays = ci.sample_indices(spec.m, 3000, seed=68)
+    ya = host(y).reshape(-1)[rays]
+    ref = oracle.project_A_rays(spec, x.astype(np.float64), rays)
+    assert rel(ya, ref) <= OP_TOL, rel(ya, ref)
+    yn = host(y).astype(np.float32)
+    vox = ci.sample_indices(spec.n, 3000, seed=69)
+    xb = host(ct.backproject_B(g, dev(yn))).reshape(-1)[vox]
+    refb = oracle.backproject_B_voxels(spec, yn.astype(np.float64), vox)
+    assert rel(xb, refb) <= OP_TOL, rel(xb, refb)
+    rows = ci.sample_indices(spec.n_views * spec.nv, 200, seed=70)
+    f = host(ct.ramp_F(g, dev(yn))).reshape(-1, spec.nu)[rows]
+    reff = oracle.ramp_F_rows(spec, yn.astype(np.float64), rows)
+    assert rel(f, reff) <= OP_TOL, rel(f, reff)
+
+
+def test_max_size_512_on_sampled_outputs(ct):
+    """The largest scan (512^3 voxels, 720 views, 768x512 detector)."""
+    spec = ci.CONE_512
+    g = ct.Geometry.from_spec(spec)
+    x = ci.random_vector(spec.n, seed=71, positive=True).astype(np.float32)
+    xd = dev(x.reshape(spec.vol_shape))
+    y = ct.project_A(g, xd)
+    del xd
+    rays = ci.sample_indices(spec.m, 1000, seed=72)
+    ya = host(y).reshape(-1)[rays]
+    ref = oracle.project_A_rays(spec, x.astype(np.float64), rays)
+    assert rel(ya, ref) <= OP_TOL, rel(ya, ref)
+    vox = ci.sample_indices(spec.n, 1000, seed=73)
+    xb = ct.backproject_B(g, y)
+    xb_s = host(xb).reshape(-1)[vox]
+    refb = oracle.backproject_B_voxels(spec, host(y).reshape(-1), vox)
+    assert rel(xb_s, refb) <= OP_TOL, rel(xb_s, refb)
+
+
+def test_operator_errors_are_reported(ct):
+    spec = ci.CONE_SMALL
+    g = ct.Geometry.from_spec(spec)
+    with pytest.raises(ValueError):
+        ct.ct_project_A(g, torch.zeros(5, device="cuda"), torch.zeros(spec.m, device="cuda"))
+    with pytest.raises(TypeError):
+        ct.ct_project_A(g, torch.zeros(spec.n, device="cuda", dtype=torch.float64),
+                        torch.zeros(spec.m, device="cuda"))
+    with pytest.raises(ct.CTError):
+        ct.ct_backproject_B(g, torch.zeros(spec.m, device="cuda"), torch.zeros(spec.n, device="cuda"), 9)
+    y = torch.zeros(spec.m, device="cuda")
+    with pytest.raises(ct.CTError):
+        ct.ct_ramp_F(g, y, y)

@@ -1,0 +1,249 @@
+"""GPU parity of the solvers (BA-GMRES, AB-GMRES, CGLS) and of the Arnoldi
+building blocks against the FP64 oracle, through the C-ABI.
+
+Tolerances: the reconstructed image and the residual history after k
+iterations agree with the FP64 oracle to relative error <= 1e-4 (residuals
+relative to resid[0]).  Full-size solves are checked through properties
+that hold at any size.
+"""
+import numpy as np
+import pytest
+import torch
+
+import ct_inputs as ci
+import oracle
+from oracle import krylov
+
+pytestmark = pytest.mark.gpu
+
+SOLVE_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ct():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2201_07408_gb300 import ct as _ct
+    return _ct
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().double().numpy()
+
+
+def data_for(spec, noise=0.01, seed=81):
+    x = ci.phantom(spec)[0].astype(np.float64)
+    b = oracle.project_A(spec, x)
+    if noise:
+        b = b + ci.gaussian_noise(b.shape, noise * b.max(), seed=seed)
+    return b.astype(np.float32), x
+
+
+CASES = [(ci.CONE_SMALL, "un", 20), (ci.CONE_SMALL, "fbp", 12), (ci.CONE_ANISO, "un", 15),
+         (ci.PAR2D_64, "un", 30), (ci.PAR2D_ANISO, "fbp", 10), (ci.CONE_512_CUT64, "un", 15)]
+
+
+@pytest.mark.parametrize("spec,b_kind,k", CASES, ids=lambda v: getattr(v, "name", str(v)))
+@pytest.mark.parametrize("dot_mode", [1, 0])
+def test_bagmres_matches_oracle(ct, spec, b_kind, k, dot_mode):
+    b, _ = data_for(spec)
+    g = ct.Geometry.from_spec(spec)
+    x, res = ct.bagmres(g, dev(b), k, b_kind=b_kind, dot_mode=dot_mode)
+    ops = oracle.Operators(spec, b_kind)
+    ref = krylov.ba_gmres(ops.A, ops.B, b.astype(np.float64).reshape(-1), k, keep_basis=False)
+    assert res.iters == k
+    assert np.max(np.abs(res.resid - ref["resid"])) <= SOLVE_TOL * ref["resid"][0]
+    assert rel(host(x), ref["x_final"]) <= SOLVE_TOL, rel(host(x), ref["x_final"])
+    assert np.all(np.diff(res.resid) <= 1e-6 * res.resid[0])
+
+
+@pytest.mark.parametrize("spec,b_kind,k", [(ci.CONE_SMALL, "un", 12), (ci.PAR2D_64, "un", 20),
+                                           (ci.CONE_ANISO, "fbp", 8)],
+                         ids=lambda v: getattr(v, "name", str(v)))
+def test_abgmres_matches_oracle(ct, spec, b_kind, k):
+    b, _ = data_for(spec)
+    g = ct.Geometry.from_spec(spec)
+    x, res = ct.abgmres(g, dev(b), k, b_kind=b_kind)
+    ops = oracle.Operators(spec, b_kind)
+    ref = krylov.ab_gmres(ops.A, ops.B, b.astype(np.float64).reshape(-1), k, keep_basis=False)
+    assert np.max(np.abs(res.resid - ref["resid"])) <= SOLVE_TOL * ref["resid"][0]
+    assert rel(host(x), ref["x_final"]) <= SOLVE_TOL, rel(host(x), ref["x_final"])
+
+
+@pytest.mark.parametrize("spec,b_kind,k", [(ci.PAR2D_64, "un", 30), (ci.CONE_SMALL, "at", 15),
+                                           (ci.CONE_SMALL, "un", 8)],
+                         ids=lambda v: getattr(v, "name", str(v)))
+def test_cgls_matches_oracle(ct, spec, b_kind, k):
+    b, _ = data_for(spec)
+    g = ct.Geometry.from_spec(spec)
+    x, res = ct.cgls(g, dev(b), k, b_kind=b_kind)
+    ops = oracle.Operators(spec, b_kind)
+    ref = krylov.cgls(ops.A, ops.B, b.astype(np.float64).reshape(-1), k)
+    assert np.max(np.abs(res.resid - ref["resid"])) <= SOLVE_TOL * ref["resid"][0]
+    assert rel(host(x), ref["x_final"]) <= SOLVE_TOL, rel(host(x), ref["x_final"])
+
+
+def test_cgls_record_data_resid(ct):
+    spec = ci.CONE_SMALL
+    b, _ = data_for(spec)
+    g = ct.Geometry.from_spec(spec)
+    x, res = ct.cgls(g, dev(b), 6, b_kind="un", record_data_resid=True)
+    ops = oracle.Operators(spec, "un")
+    ref = krylov.cgls(ops.A, ops.B, b.astype(np.float64).reshape(-1), 6, record_data_resid=True)
+    assert np.max(np.abs(res.resid - ref["data_resid"])) <= SOLVE_TOL * ref["data_resid"][0]
+
+
+def test_unmatched_cgls_diverges_on_gpu(ct):
+    """Sec. III: CGLS with (A, B_un) reaches a minimum data residual and
+    then grows, while BA-GMRES keeps lowering ||BAx - Bb||."""
+    spec = ci._cone("tinycone", 8, 10.0, 12, 13, 9, 14.0, ang0=0.2)
+    x = ci.random_vector(spec.n, 1, positive=True)
+    b = oracle.project_A(spec, x).astype(np.float32)
+    g = ct.Geometry.from_spec(spec)
+    _, res = ct.cgls(g, dev(b), 50, b_kind="un", record_data_resid=True)
+    r = res.resid[:res.iters + 1]
+    jmin = int(np.argmin(r))
+    assert 0 < jmin < 40 and r[-1] > 10 * r[jmin]
+    _, ba = ct.bagmres(g, dev(b), 40)
+    assert np.all(np.diff(ba.resid[:ba.iters + 1]) <= 1e-6 * ba.resid[0])
+
+
+def test_zero_data_is_a_lucky_breakdown(ct):
+    spec = ci.CONE_ANISO
+    g = ct.Geometry.from_spec(spec)
+    x = torch.full(spec.vol_shape, 7.0, device="cuda")
+    res = ct.ct_bagmres_solve(g, torch.zeros(spec.sino_shape, device="cuda"), 5, x)
+    assert res.status == ct.CT_BREAKDOWN_LUCKY and res.iters == 0
+    assert torch.count_nonzero(x) == 0
+    assert res.resid[0] == 0.0 and np.all(res.resid[1:] == -1.0)
+
+
+def test_full_dimension_reaches_exact_solution(ct):
+    """Consistent data for a 2D problem with n = 4 unknowns: after n
+    iterations the Krylov space is the whole space and BA-GMRES returns the
+    exact solution of BAx = Bb, here x_true."""
+    spec = ci.Geometry("n4", ci.PARALLEL_2D, 2, 2, 1, 1.0, 6, 0.0, np.pi, 5, 1, 1.0, 1.0)
+    xt = np.array([1.0, 2.0, 0.5, 3.0])
+    b = oracle.project_A(spec, xt).astype(np.float32)
+    g = ct.Geometry.from_spec(spec)
+    x = torch.empty(spec.vol_shape, device="cuda")
+    res = ct.ct_bagmres_solve(g, dev(b), 4, x)
+    assert res.iters == 4
+    assert res.status in (ct.CT_BREAKDOWN_LUCKY, ct.CT_OK)
+    assert rel(host(x), xt) < 1e-4
+    assert res.resid[4] <= 1e-5 * res.resid[0]
+
+
+def test_tolerance_stop(ct):
+    spec = ci.CONE_SMALL
+    b, _ = data_for(spec)
+    g = ct.Geometry.from_spec(spec)
+    x, res = ct.bagmres(g, dev(b), 30, tol=0.05)
+    assert 0 < res.iters < 30
+    assert res.resid[res.iters] <= 0.05 * res.resid[0] < res.resid[res.iters - 1]
+    assert np.all(res.resid[res.iters + 1:] == -1.0)
+    x2, res2 = ct.bagmres(g, dev(b), res.iters)
+    assert torch.equal(x, x2)
+
+
+def test_workspace_and_determinism(ct):
+    spec = ci.CONE_SMALL
+    b, _ = data_for(spec)
+    g = ct.Geometry.from_spec(spec)
+    bd = dev(b)
+    x1 = torch.empty(spec.vol_shape, device="cuda")
+    x2 = torch.empty(spec.vol_shape, device="cuda")
+    r1 = ct.ct_bagmres_solve(g, bd, 10, x1, ct.make_opts(b_kind="fbp"), workspace="torch")
+    r2 = ct.ct_bagmres_solve(g, bd, 10, x2, ct.make_opts(b_kind="fbp"), workspace=None)
+    assert torch.equal(x1, x2) and np.array_equal(r1.resid, r2.resid)
+    small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ct.CTError) as ei:
+        ct.ct_bagmres_solve(g, bd, 10, x1, ct.make_opts(workspace=small), workspace=None)
+    assert ei.value.status == ct.CT_ENOMEM
+
+
+def test_reorthogonalisation_keeps_parity(ct):
+    spec = ci.CONE_SMALL
+    b, _ = data_for(spec)
+    g = ct.Geometry.from_spec(spec)
+    x, res = ct.bagmres(g, dev(b), 20, reorth=1)
+    ops = oracle.Operators(spec, "un")
+    ref = krylov.ba_gmres(ops.A, ops.B, b.astype(np.float64).reshape(-1), 20, keep_basis=False)
+    assert rel(host(x), ref["x_final"]) <= SOLVE_TOL
+    assert np.max(np.abs(res.resid - ref["resid"])) <= SOLVE_TOL * ref["resid"][0]
+
+
+@pytest.mark.parametrize("dot_mode", [0, 1])
+@pytest.mark.parametrize("length", [1, 1000, 1 << 20, (1 << 20) + 3])
+def test_mgs_sweep_against_definition(ct, dot_mode, length):
+    """One MGS sweep equals the textbook recurrence h_i = <q, v_i>,
+    q -= h_i v_i (FP64 numpy), then h_j = ||q||."""
+    j = 6
+    rng = np.random.default_rng(90 + length % 7)
+    Q, _ = np.linalg.qr(rng.standard_normal((length, j))) if length >= j else (
+        rng.standard_normal((length, j)), None)
+    ldv = length + (64 - length % 64) % 64
+    V = np.zeros((j, ldv), dtype=np.float32)
+    V[:, :length] = Q.T.astype(np.float32)
+    q0 = rng.standard_normal(length).astype(np.float32) + 0.5 * V[0, :length]
+    qd = dev(q0)
+    h = torch.zeros(j + 1, dtype=torch.float64, device="cuda")
+    ct.ct_mgs_sweep(dev(V), ldv, j, length, qd, h, dot_mode)
+    q = q0.astype(np.float64).copy()
+    href = np.zeros(j + 1)
+    for i in range(j):
+        href[i] = q @ V[i, :length].astype(np.float64)
+        q -= href[i] * V[i, :length].astype(np.float64)
+    href[j] = np.linalg.norm(q)
+    hg = host(h)
+    assert np.max(np.abs(hg - href)) <= 1e-5 * np.linalg.norm(q0)
+    assert rel(host(qd), q) <= 1e-5
+
+
+def test_basis_combine_against_definition(ct):
+    k, length = 9, 123457
+    rng = np.random.default_rng(95)
+    ldv = length + 11
+    V = rng.standard_normal((k, ldv)).astype(np.float32)
+    y = rng.standard_normal(k)
+    x = torch.empty(length, device="cuda")
+    ct.ct_basis_combine(dev(V), ldv, k, length, torch.from_numpy(y).cuda(), x)
+    ref = (y[:, None] * V[:, :length].astype(np.float64)).sum(axis=0)
+    assert rel(host(x), ref) <= 1e-6
+
+
+@pytest.mark.parametrize("b_kind,k", [("fbp", 40), ("un", 20)])
+def test_full_size_256_bagmres_properties(ct, b_kind, k):
+    """The 256^3 headline solve (Poisson data): the residual history is
+    non-increasing, its last entry matches the recomputed ||B(b - A x_k)||,
+    and the first iterations agree with the oracle's closed forms: resid[0]
+    = ||B b|| and resid[1] = min_c ||B b - c B A B b|| (one-dimensional
+    least squares)."""
+    spec = ci.CONE_256
+    g = ct.Geometry.from_spec(spec)
+    x_true = ci.phantom(spec)[0]
+    p = host(ct.project_A(g, dev(x_true)))
+    b = dev(ci.poisson_log_data(p, seed=1))
+    x, res = ct.bagmres(g, b, k, b_kind=b_kind)
+    r = res.resid
+    assert res.iters == k
+    assert np.all(np.diff(r) <= 1e-6 * r[0])
+    Bb = ct.backproject_B(g, b, b_kind).double()
+    true = float(torch.linalg.vector_norm(Bb - ct.backproject_B(g, ct.project_A(g, x), b_kind).double()))
+    assert abs(true - r[-1]) <= 2e-3 * r[0], (true, r[-1])
+    assert abs(float(torch.linalg.vector_norm(Bb)) - r[0]) <= 1e-6 * r[0]
+    s1 = ct.backproject_B(g, ct.project_A(g, Bb.float()), b_kind).double()
+    c = float((s1 * Bb).sum() / (s1 * s1).sum())
+    r1 = float(torch.linalg.vector_norm(Bb - c * s1))
+    assert abs(r1 - r[1]) <= 1e-4 * r[0], (r1, r[1])
