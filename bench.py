@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--workload", default=ci.CONE_256.name)
     ap.add_argument("--iters", type=int, default=K_ITERS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--op", default=None, choices=["A", "B", "Bfbp", "F", "At", "Bt", "mgs"],
+                    help="time one operator of the workload instead of the solve (profiling aid)")
     return ap.parse_args()
 
 
@@ -348,7 +350,7 @@ def run_ours(args, world, rank, local):
             "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": int(spec.m * 4),
                     "d2h_bytes_per_step": int(spec.n * 4 + (k + 1) * 8)}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = oracle_iteration_sample(spec, x_true, b_host, k)
+        cb = oracle_iteration_sample(spec, x_true, b_host, k, frac=0.5)
         # relative error of the GPU operators on the oracle's samples
         a_gpu = p.reshape(-1)[torch.from_numpy(cb["rays"]).to(dev)].double().cpu().numpy()
         bu = ct.backproject_B(g, b, "un").reshape(-1)[torch.from_numpy(cb["vox"]).to(dev)]
@@ -365,9 +367,63 @@ def run_ours(args, world, rank, local):
         torch.distributed.destroy_process_group()
 
 
+def run_op(args):
+    """Times one operator of the workload: W untimed launches, then K timed
+    ones (CUDA events on the launching stream)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2201_07408_gb300 import ct
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    spec = ci.WORKLOADS[args.workload]
+    g = ct.Geometry.from_spec(spec, device=dev)
+    x = torch.from_numpy(make_inputs(spec)).to(dev)
+    y = ct.project_A(g, x)
+    out_v = torch.empty(spec.vol_shape, device=dev)
+    out_s = torch.empty(spec.sino_shape, device=dev)
+    j = 20
+    V = q = h = None
+    if args.op == "mgs":
+        ldv = (spec.n + 63) // 64 * 64
+        V = torch.randn(j * ldv, device=dev) / math.sqrt(spec.n)
+        q = torch.randn(spec.n, device=dev)
+        h = torch.zeros(j + 1, dtype=torch.float64, device=dev)
+    fn = {"A": lambda: ct.ct_project_A(g, x, out_s),
+          "B": lambda: ct.ct_backproject_B(g, y, out_v, "un"),
+          "Bfbp": lambda: ct.ct_backproject_B(g, y, out_v, "fbp"),
+          "F": lambda: ct.ct_ramp_F(g, y, out_s),
+          "At": lambda: ct.ct_adjoint_At(g, y, out_v),
+          "Bt": lambda: ct.ct_adjoint_Bt(g, x, out_s, "un"),
+          "mgs": lambda: ct.ct_mgs_sweep(V, (spec.n + 63) // 64 * 64, j, spec.n, q, h)}[args.op]
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    ct.profile_reset()
+    ct.profile_enable(True)
+    st = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ct.profile_enable(False)
+    prof = {k: v for k, v in ct.profile_read().items() if v[1]}
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"op": args.op, "workload": spec.name, "ms_per_call": round(ms, 4),
+                      "kernels": {k: {"ms_per_launch": round(v[0] / v[1], 4), "launches": v[1]}
+                                  for k, v in prof.items()},
+                      "joseph_samples": spec.joseph_samples(), "voxel_view_samples": spec.voxel_view_samples()}),
+          flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
+    if args.op:
+        run_op(args)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
         return

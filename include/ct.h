@@ -93,8 +93,9 @@ typedef struct ct_geom ct_geom;
 typedef struct {
     int b_kind;              /* ct_b_kind; default CT_B_UN */
     double tol;              /* stop when resid[j] <= tol*resid[0]; 0 = run all k */
-    int dot_mode;            /* Arnoldi inner products: 0 = FP32 with compensated (two-sum)
-                                accumulation, 1 = FP32 products, FP64 reduction (default) */
+    int dot_mode;            /* Arnoldi inner products: 0 = compensated FP32 accumulation (FMA
+                                two-product + two-sum) then FP64 reduction (default),
+                                1 = plain FP32 FMA accumulation then FP64 reduction */
     int reorth;              /* 0 = one MGS sweep (default), 1 = a second sweep when the
                                 norm drops below 1/sqrt(2) of its value before the sweep */
     int record_data_resid;   /* CGLS only: resid holds the recomputed ||b - A x_j|| */

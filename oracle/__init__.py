@@ -227,7 +227,7 @@ class Operators:
         return project_A(self.g, x).reshape(-1)
 
     def B(self, y):
-        if self.b_kind == "At":
+        if self.b_kind in ("At", "at"):
             return adjoint_At(self.g, y).reshape(-1)
         return backproject_B(self.g, y, filtered=self.b_kind == "fbp").reshape(-1)
 

@@ -57,12 +57,45 @@ cudaError_t launch_pad_sino(const GeomDev &g, float *src, const double *scale, b
 }
 
 // ---------------------------------------------------------------------------
-// Ramp filter.  One block per detector row: the cosine-weighted row sits in
-// shared memory between nu zeros on either side, so the linear convolution
-// with the (symmetric, odd-tap) Ram-Lak kernel needs no bounds tests.
-// F^T applies the cosine weight after the convolution instead of before.
+// Ramp filter.  The Ram-Lak kernel is zero at even nonzero offsets, so each
+// output parity only sees samples of the other parity:
+//   out[2i]   = h0 E[i] + sum_m g[m] (O[i-m-1] + O[i+m])
+//   out[2i+1] = h0 O[i] + sum_m g[m] (E[i-m]   + E[i+m+1])
+// with E, O the even / odd samples of the (cosine-weighted) row and
+// g[m] = h[2m+1].  A thread computes RAMP_R consecutive outputs of one
+// parity with two register windows that slide by one sample per tap, so
+// each tap costs two shared-memory loads for 2*RAMP_R FADD/FFMA; RAMP_R is
+// odd so that the window loads of neighbouring threads fall in distinct
+// banks.  Rows sit in shared memory with zero margins, so no load is
+// bounds-tested.  F^T weights the output instead of the input.
 // ---------------------------------------------------------------------------
-constexpr int RAMP_BLOCK = 128;
+constexpr int RAMP_R = 9;
+
+struct RampShape {
+    int M;       // taps g[0..M-1]
+    int nhE, nhO;
+    int off;     // index of sample 0 inside a half-row array
+    int len;     // length of one half-row array
+    int tpr;     // threads per row
+    int rows;    // rows per block
+    int threads;
+    size_t smem;
+};
+
+static RampShape ramp_shape(int nu)
+{
+    RampShape r;
+    r.M = nu / 2;
+    r.nhE = (nu + 1) / 2;
+    r.nhO = nu / 2;
+    r.off = r.M + 1;
+    r.len = r.off + r.nhE + RAMP_R + r.M + 2;
+    r.tpr = (r.nhE + RAMP_R - 1) / RAMP_R + (r.nhO + RAMP_R - 1) / RAMP_R;
+    r.rows = r.tpr >= 256 ? 1 : 256 / r.tpr;
+    r.threads = ((r.tpr * r.rows + 31) / 32) * 32;
+    r.smem = sizeof(float) * (size_t(r.M) + size_t(r.rows) * 2 * r.len);
+    return r;
+}
 
 __device__ __forceinline__ float cosine_weight(const GeomDev &g, int iu, int iv)
 {
@@ -72,48 +105,114 @@ __device__ __forceinline__ float cosine_weight(const GeomDev &g, int iu, int iv)
     return g.sdd / sqrtf(fmaf(g.sdd, g.sdd, fmaf(u, u, v * v)));
 }
 
-__global__ void __launch_bounds__(RAMP_BLOCK) ramp_kernel(GeomDev g, const float *__restrict__ src,
-                                                          float *__restrict__ dst, SinoLayout lay,
-                                                          int transpose,
-                                                          const int *__restrict__ stop)
+// acc[j] = h0 C[i0+j] + sum_m g[m] (L[i0+j-m-AL] + Rr[i0+j+m+AR]), L == Rr
+template <int AL, int AR>
+__device__ __forceinline__ void ramp_conv(const float *__restrict__ L, const float *__restrict__ C,
+                                          const float *__restrict__ gm, int M, int i0, float h0,
+                                          float (&acc)[RAMP_R])
+{
+    float Lw[RAMP_R], Rw[RAMP_R];
+#pragma unroll
+    for (int j = 0; j < RAMP_R; ++j) {
+        Lw[j] = L[i0 + j + 1 - AL];
+        Rw[j] = L[i0 + j - 1 + AR];
+        acc[j] = h0 * C[i0 + j];
+    }
+    int m = 0;
+    for (; m + RAMP_R <= M; m += RAMP_R) {
+#pragma unroll
+        for (int t = 0; t < RAMP_R; ++t) {
+            const int mm = m + t;
+#pragma unroll
+            for (int j = RAMP_R - 1; j > 0; --j) Lw[j] = Lw[j - 1];
+            Lw[0] = L[i0 - mm - AL];
+#pragma unroll
+            for (int j = 0; j < RAMP_R - 1; ++j) Rw[j] = Rw[j + 1];
+            Rw[RAMP_R - 1] = L[i0 + RAMP_R - 1 + mm + AR];
+            const float gv = gm[mm];
+#pragma unroll
+            for (int j = 0; j < RAMP_R; ++j) acc[j] = fmaf(gv, Lw[j] + Rw[j], acc[j]);
+        }
+    }
+    for (; m < M; ++m) {
+#pragma unroll
+        for (int j = RAMP_R - 1; j > 0; --j) Lw[j] = Lw[j - 1];
+        Lw[0] = L[i0 - m - AL];
+#pragma unroll
+        for (int j = 0; j < RAMP_R - 1; ++j) Rw[j] = Rw[j + 1];
+        Rw[RAMP_R - 1] = L[i0 + RAMP_R - 1 + m + AR];
+        const float gv = gm[m];
+#pragma unroll
+        for (int j = 0; j < RAMP_R; ++j) acc[j] = fmaf(gv, Lw[j] + Rw[j], acc[j]);
+    }
+}
+
+__global__ void ramp_kernel(GeomDev g, RampShape rs, const float *__restrict__ src, float *__restrict__ dst,
+                            SinoLayout lay, int transpose, const int *__restrict__ stop)
 {
     if (stop && *stop) return;
     extern __shared__ float sm[];
     const int nu = g.nu;
-    float *row = sm;            // 3 nu: [zeros | weighted row | zeros]
-    float *taps = sm + 3 * nu;  // nu
-    const int r = blockIdx.x;   // s*nv + iv
-    const int iv = r % g.nv;
-    const int s = r / g.nv;
-    const float *in = src + size_t(r) * nu;
-    for (int i = threadIdx.x; i < nu; i += RAMP_BLOCK) {
-        const float w = transpose ? 1.0f : cosine_weight(g, i, iv);
-        row[i] = 0.0f;
-        row[nu + i] = in[i] * w;
-        row[2 * nu + i] = 0.0f;
-        taps[i] = g.ramp_taps[i];
+    const int nrows = g.n_views * g.nv;
+    float *gm = sm;                                   // taps g[m] = h[2m+1]
+    const int row_base = blockIdx.x * rs.rows;
+    for (int i = threadIdx.x; i < rs.M; i += blockDim.x) gm[i] = g.ramp_taps[2 * i + 1];
+    // half rows with zero margins
+    for (int i = threadIdx.x; i < rs.rows * 2 * rs.len; i += blockDim.x) sm[rs.M + i] = 0.0f;
+    __syncthreads();
+    for (int i = threadIdx.x; i < rs.rows * nu; i += blockDim.x) {
+        const int lr = i / nu, iu = i - lr * nu;
+        const int r = row_base + lr;
+        if (r >= nrows) continue;
+        const int iv = r % g.nv;
+        const float w = transpose ? 1.0f : cosine_weight(g, iu, iv);
+        float *E = sm + rs.M + size_t(lr) * 2 * rs.len + rs.off;
+        float *O = E + rs.len;
+        (iu & 1 ? O : E)[iu >> 1] = src[size_t(r) * nu + iu] * w;
     }
     __syncthreads();
+    const int lr = threadIdx.x / rs.tpr;
+    const int tile = threadIdx.x - lr * rs.tpr;
+    const int r = row_base + lr;
+    if (lr >= rs.rows || r >= nrows) return;
+    const int iv = r % g.nv;
+    const int s = r / g.nv;
+    const float *E = sm + rs.M + size_t(lr) * 2 * rs.len + rs.off;
+    const float *O = E + rs.len;
+    const int tilesE = (rs.nhE + RAMP_R - 1) / RAMP_R;
+    const int parity = tile < tilesE ? 0 : 1;
+    const int i0 = (parity ? tile - tilesE : tile) * RAMP_R;
+    const float h0 = g.ramp_taps[0];
+    float acc[RAMP_R];
+    if (parity == 0)
+        ramp_conv<1, 0>(O, E, gm, rs.M, i0, h0, acc);
+    else
+        ramp_conv<0, 1>(E, O, gm, rs.M, i0, h0, acc);
+    const int nh = parity ? rs.nhO : rs.nhE;
     float *out = dst + (size_t(s) * lay.rows_per_view + iv + lay.row_off) * lay.pitch + lay.col_off;
-    for (int i = threadIdx.x; i < nu; i += RAMP_BLOCK) {
-        const float *c = row + nu + i;
-        float acc = taps[0] * c[0];
-        for (int k = 1; k < nu; k += 2) acc = fmaf(taps[k], c[-k] + c[k], acc);
-        out[i] = transpose ? acc * cosine_weight(g, i, iv) : acc;
+#pragma unroll
+    for (int j = 0; j < RAMP_R; ++j) {
+        const int i = i0 + j;
+        if (i < nh) {
+            const int iu = 2 * i + parity;
+            out[iu] = transpose ? acc[j] * cosine_weight(g, iu, iv) : acc[j];
+        }
     }
 }
 
 cudaError_t launch_ramp(const GeomDev &g, const float *src, float *dst, SinoLayout lay, bool transpose,
                         const int *stop, cudaStream_t st)
 {
-    const size_t smem = size_t(4) * g.nu * sizeof(float);
-    if (smem > 48 * 1024) {
+    const RampShape rs = ramp_shape(g.nu);
+    if (rs.smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(ramp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(smem));
+                                             int(rs.smem));
         if (e != cudaSuccess) return e;
     }
+    const int nrows = g.n_views * g.nv;
+    const unsigned blocks = unsigned((nrows + rs.rows - 1) / rs.rows);
     ProfScope prof(PK_RAMP, st);
-    ramp_kernel<<<g.n_views * g.nv, RAMP_BLOCK, smem, st>>>(g, src, dst, lay, transpose ? 1 : 0, stop);
+    ramp_kernel<<<blocks, rs.threads, rs.smem, st>>>(g, rs, src, dst, lay, transpose ? 1 : 0, stop);
     return cudaGetLastError();
 }
 

@@ -98,7 +98,7 @@ void ct_solve_opts_default(ct_solve_opts *o)
     std::memset(o, 0, sizeof(*o));
     o->b_kind = CT_B_UN;
     o->tol = 0.0;
-    o->dot_mode = 1;
+    o->dot_mode = 0;
     o->reorth = 0;
     o->record_data_resid = 0;
     o->workspace = nullptr;

@@ -207,7 +207,7 @@ def ct_ramp_F(geom: Geometry, y, yf, transpose=False, stream=None):
                                         int(bool(transpose)), _stream(stream, d)))
 
 
-def make_opts(b_kind=CT_B_UN, tol=0.0, dot_mode=1, reorth=0, record_data_resid=False, workspace=None):
+def make_opts(b_kind=CT_B_UN, tol=0.0, dot_mode=0, reorth=0, record_data_resid=False, workspace=None):
     o = ct_solve_opts()
     lib().ct_solve_opts_default(ctypes.byref(o))
     o.b_kind = _bkind(b_kind)
@@ -269,7 +269,7 @@ def ct_cgls_solve(geom, b, k, x_out, opts=None, stream=None, workspace="torch") 
                   workspace)
 
 
-def ct_mgs_sweep(V, ldv, j, length, q, h, dot_mode=1, stream=None):
+def ct_mgs_sweep(V, ldv, j, length, q, h, dot_mode=0, stream=None):
     """One MGS sweep of q against j basis vectors stored with stride ldv in V;
     h (float64 CUDA tensor of j+1) receives the coefficients and ||q||."""
     if h.dtype != torch.float64 or not h.is_cuda or h.numel() < j + 1:
@@ -343,14 +343,14 @@ def ramp_F(geom, y, transpose=False, stream=None):
     return out
 
 
-def bagmres(geom, b, k, b_kind="un", tol=0.0, dot_mode=1, reorth=0, stream=None):
+def bagmres(geom, b, k, b_kind="un", tol=0.0, dot_mode=0, reorth=0, stream=None):
     x = torch.empty(geom.vol_shape, dtype=torch.float32, device=geom.device)
     res = ct_bagmres_solve(geom, b.contiguous(), k, x,
                            make_opts(b_kind=b_kind, tol=tol, dot_mode=dot_mode, reorth=reorth), stream)
     return x, res
 
 
-def abgmres(geom, b, k, b_kind="un", tol=0.0, dot_mode=1, reorth=0, stream=None):
+def abgmres(geom, b, k, b_kind="un", tol=0.0, dot_mode=0, reorth=0, stream=None):
     x = torch.empty(geom.vol_shape, dtype=torch.float32, device=geom.device)
     res = ct_abgmres_solve(geom, b.contiguous(), k, x,
                            make_opts(b_kind=b_kind, tol=tol, dot_mode=dot_mode, reorth=reorth), stream)

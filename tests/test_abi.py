@@ -48,7 +48,7 @@ def test_version_and_defaults(libct):
     assert "sm_103a" in libct.version()
     o = libct.ct_solve_opts()
     libct.lib().ct_solve_opts_default(ctypes.byref(o))
-    assert o.b_kind == libct.CT_B_UN and o.dot_mode == 1 and o.reorth == 0 and o.tol == 0.0
+    assert o.b_kind == libct.CT_B_UN and o.dot_mode == 0 and o.reorth == 0 and o.tol == 0.0
     assert not o.workspace
 
 
