@@ -161,6 +161,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_over_ranks(elapsed_s, iters, world, device=None):
+    """Whole-job throughput of replicated solves: the slowest rank's time and
+    the iterations summed over ranks (one all-reduce each; works with the
+    nccl and gloo backends)."""
+    import torch
+    t = torch.tensor([float(elapsed_s)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    elapsed_max = float(t.item())
+    return elapsed_max, float(n.item()), float(n.item()) / elapsed_max
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -270,13 +285,7 @@ def run_ours(args, world, rank, local):
     ct.profile_enable(False)
     prof = ct.profile_read()
     elapsed = e0.elapsed_time(e1) / 1e3
-    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-    tot = torch.tensor([float(iters_done)], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.SUM)
-    elapsed_max = float(t.item())
-    value = float(tot.item()) / elapsed_max
+    elapsed_max, _, value = aggregate_over_ranks(elapsed, iters_done, world, dev)
     clocks = clk.summary()
 
     # per-kernel figures from the library's event pairs over the timed region

@@ -251,27 +251,48 @@ __device__ __forceinline__ ColumnView column_view(const GeomDev &g, int s, float
     return c;
 }
 
+// A block owns a 32 x 32 tile of (x, y) columns and B_ZC consecutive z.
+// Which of x or y its lanes run along is chosen per view: along x when the
+// detector coordinate u moves faster with x than with y (|tx| >= |ty|),
+// else along y.  Along that axis neighbouring voxels land on neighbouring
+// detector pixels of the same rows; along the other axis the magnification
+// changes, so neighbouring voxels would read different rows.  The two
+// partial sums (x-lane views and y-lane views) meet in shared memory.
+constexpr int B_TILE = 32;
+constexpr int B_ZC = 8;
+
 template <int ZC>
-__global__ void __launch_bounds__(B_BX *B_BY) voxel_B_kernel(GeomDev g, const float *__restrict__ ypad,
-                                                             float *__restrict__ x,
-                                                             const int *__restrict__ stop)
+__global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, const float *__restrict__ ypad,
+                                                                 float *__restrict__ x,
+                                                                 const int *__restrict__ stop)
 {
     if (stop && *stop) return;
-    const int ix = blockIdx.x * B_BX + threadIdx.x;
-    const int iy = blockIdx.y * B_BY + threadIdx.y;
+    __shared__ float tile[ZC][B_TILE][B_TILE + 1];
+    const int l = threadIdx.x, w = threadIdx.y;
+    const int X0 = blockIdx.x * B_TILE, Y0 = blockIdx.y * B_TILE;
     const int iz0 = blockIdx.z * ZC;
-    if (ix >= g.nx || iy >= g.ny) return;
-    const float xc = (float(ix) - g.cx) * g.vox;
-    const float yc = (float(iy) - g.cy) * g.vox;
     const float zfirst = (float(iz0) - g.cz) * g.vox;
+    // column of the x-lane mapping and of the y-lane mapping (clamped into the grid;
+    // columns past the edge compute throw-away values)
+    const int ax = min(X0 + l, g.nx - 1), ay = min(Y0 + w, g.ny - 1);
+    const int bx = min(X0 + w, g.nx - 1), by = min(Y0 + l, g.ny - 1);
+    const float axc = (float(ax) - g.cx) * g.vox, ayc = (float(ay) - g.cy) * g.vox;
+    const float bxc = (float(bx) - g.cx) * g.vox, byc = (float(by) - g.cy) * g.vox;
     const int view_stride = g.nvp * g.pitchU;
-    float acc[ZC];
+    float accA[ZC], accB[ZC];
 #pragma unroll
-    for (int k = 0; k < ZC; ++k) acc[k] = 0.0f;
+    for (int k = 0; k < ZC; ++k) {
+        accA[k] = 0.0f;
+        accB[k] = 0.0f;
+    }
     for (int s = 0; s < g.n_views; ++s) {
-        const ColumnView c = column_view(g, s, xc, yc, zfirst);
+        const float4 *vp = reinterpret_cast<const float4 *>(g.viewB + s);
+        const float tx = __ldg(&vp->w), ty = __ldg(&(vp + 1)->x);
+        const bool xl = fabsf(tx) >= fabsf(ty);   // uniform over the block
+        const ColumnView c = xl ? column_view(g, s, axc, ayc, zfirst) : column_view(g, s, bxc, byc, zfirst);
         if (c.skip) continue;
         const float *vbase = ypad + size_t(s) * view_stride + c.col;
+        float r[ZC];
 #pragma unroll
         for (int k = 0; k < ZC; ++k) {
             const float fv = fmaf(float(k), c.gv, c.fv0);
@@ -281,27 +302,42 @@ __global__ void __launch_bounds__(B_BX *B_BY) voxel_B_kernel(GeomDev g, const fl
             const float *rowp = vbase + (v0 + PAD_V) * g.pitchU;
             const float r0 = fmaf(c.a0, __ldg(rowp), c.a1 * __ldg(rowp + 1));
             const float r1 = fmaf(c.a0, __ldg(rowp + g.pitchU), c.a1 * __ldg(rowp + g.pitchU + 1));
-            acc[k] += fmaf(wv, r1 - r0, r0);
+            r[k] = fmaf(wv, r1 - r0, r0);
+        }
+        if (xl) {
+#pragma unroll
+            for (int k = 0; k < ZC; ++k) accA[k] += r[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < ZC; ++k) accB[k] += r[k];
         }
     }
+    // x-lane sums belong to (x = X0 + l, y = Y0 + w), y-lane sums to (x = X0 + w, y = Y0 + l)
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) tile[k][w][l] = accA[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) tile[k][l][w] += accB[k];
+    __syncthreads();
+    const int ix = X0 + l, iy = Y0 + w;
+    if (ix >= g.nx || iy >= g.ny) return;
 #pragma unroll
     for (int k = 0; k < ZC; ++k) {
         const int iz = iz0 + k;
-        if (iz < g.nz) x[(size_t(iz) * g.ny + iy) * g.nx + ix] = acc[k];
+        if (iz < g.nz) x[(size_t(iz) * g.ny + iy) * g.nx + ix] = tile[k][w][l];
     }
 }
 
 cudaError_t launch_voxel_B(const GeomDev &g, const float *ypad, float *x, const int *stop, cudaStream_t st)
 {
     ProfScope prof(PK_VOXEL_B, st);
-    dim3 block(B_BX, B_BY);
+    dim3 block(B_TILE, B_TILE);
     if (g.nz == 1) {
-        dim3 grid((g.nx + B_BX - 1) / B_BX, (g.ny + B_BY - 1) / B_BY, 1);
+        dim3 grid((g.nx + B_TILE - 1) / B_TILE, (g.ny + B_TILE - 1) / B_TILE, 1);
         voxel_B_kernel<1><<<grid, block, 0, st>>>(g, ypad, x, stop);
     } else {
-        constexpr int ZC = 8;
-        dim3 grid((g.nx + B_BX - 1) / B_BX, (g.ny + B_BY - 1) / B_BY, (g.nz + ZC - 1) / ZC);
-        voxel_B_kernel<ZC><<<grid, block, 0, st>>>(g, ypad, x, stop);
+        dim3 grid((g.nx + B_TILE - 1) / B_TILE, (g.ny + B_TILE - 1) / B_TILE, (g.nz + B_ZC - 1) / B_ZC);
+        voxel_B_kernel<B_ZC><<<grid, block, 0, st>>>(g, ypad, x, stop);
     }
     return cudaGetLastError();
 }

@@ -146,60 +146,148 @@ cudaError_t launch_plane_copies(const GeomDev &g, float *vol, const double *scal
 }
 
 // ---------------------------------------------------------------------------
-// y = A x.  One thread per ray, rays of a detector row on neighbouring lanes.
+// y = A x.
+//
+// One thread walks A_VR rays of one detector column: same view and u,
+// consecutive v.  On a flat detector those rays share d_x, d_y and the cross
+// product, hence the dominant axis and the in-plane coordinate f_b(p) of every
+// plane; only z differs, f_z(p, v) = cz + gz(v) (p - c_a - S_a/vox), with
+// gz(v) = v dzv / d_a.  Per plane the thread interpolates along b once per
+// z-row it needs and keeps a two-row window (rows zc, zc+1) that slides up as
+// v increases (z is monotone in v along a column), so most rays cost one new
+// row pair instead of two.  Lanes are consecutive u of one detector row
+// segment and walk a warp-uniform plane range, so a warp's loads of one plane
+// fall in a few consecutive sectors.  Samples outside a ray's own range have
+// their row / column clamped into the zero border and add exactly zero.
 // ---------------------------------------------------------------------------
 constexpr int A_BLOCK = 128;
 
+template <int VR>
 __global__ void __launch_bounds__(A_BLOCK) joseph_A_kernel(GeomDev g, const float *__restrict__ Xc,
                                                            const float *__restrict__ Yc,
                                                            float *__restrict__ y, SinoLayout lay,
                                                            const int *__restrict__ stop)
 {
     if (stop && *stop) return;
-    const int ray = blockIdx.x * A_BLOCK + threadIdx.x;
-    const int per_view = g.nu * g.nv;
-    if (ray >= per_view * g.n_views) return;
-    const int s = ray / per_view;
-    const int rem = ray - s * per_view;
-    const int iv = rem / g.nu;
-    const int iu = rem - iv * g.nu;
-    const RaySetup r = ray_setup(g, s, iv, iu);
+    const int lane_u = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int iv0 = (blockIdx.y * (A_BLOCK / 32) + (threadIdx.x >> 5)) * VR;
+    const int s = blockIdx.z;
+    const bool live = lane_u < g.nu && iv0 < g.nv;
+    const int iu = min(lane_u, g.nu - 1);
+    const int ivl = min(iv0 + VR - 1, g.nv - 1);
 
-    const float *__restrict__ base = r.xdom ? Xc : Yc;
-    const int Na = r.xdom ? g.nx : g.ny;
-    const int pitch = r.xdom ? g.pitchX : g.pitchY;
-    const int zstride = Na * pitch;            // one padded z slice
-    // element offset of (zp = PAD_A + z0, plane p, bp = PAD_A + b0) = (z0*Na + p)*pitch + b0 + off0
-    const int off0 = (PAD_A * Na) * pitch + PAD_A;
+    // geometry shared by the column's rays
+    const float4 *vp = reinterpret_cast<const float4 *>(g.viewA + s);
+    const float4 a = __ldg(vp), b = __ldg(vp + 1);   // (dx0, dxu, dy0, dyu), (dzv, crossu, sx, sy)
+    const float u = (float(iu) - g.cu) * g.du;
+    const float dx = fmaf(u, a.y, a.x);
+    const float dy = fmaf(u, a.w, a.z);
+    const float cross = u * b.y;
+    const bool xdom = fabsf(dx) >= fabsf(dy);
+    const float da = xdom ? dx : dy;
+    const float inv_da = 1.0f / da;
+    const int Na = xdom ? g.nx : g.ny;
+    const int Nb = xdom ? g.ny : g.nx;
+    const float ca = xdom ? g.cx : g.cy;
+    const float gb = (xdom ? dy : dx) * inv_da;
+    const float cterm = cross * inv_da * g.inv_vox;
+    const float fbc = xdom ? g.cy - cterm : g.cx + cterm;
+    const float Sv = (xdom ? b.z : b.w) * g.inv_vox;   // source coordinate along the axis, in voxels
+    const float gz_step = g.dv * b.x * inv_da;           // d gz / d iv
+    const float gz0 = (float(iv0) - g.cv) * gz_step;     // gz of the first ray
 
-    float acc = 0.0f;
-#pragma unroll 4
-    for (int p = r.p0; p <= r.p1; ++p) {
-        const float pm = float(p) - r.ca;
-        const float fb = fmaf(pm, r.gb, r.fbc);
-        const float fz = fmaf(pm, r.gz, r.fzc);
-        const float b0f = floorf(fb), z0f = floorf(fz);
-        const float wb = fb - b0f, wz = fz - z0f;
-        const int idx = (int(z0f) * Na + p) * pitch + int(b0f) + off0;
-        const float v00 = __ldg(base + idx);
-        const float v01 = __ldg(base + idx + 1);
-        const float v10 = __ldg(base + idx + zstride);
-        const float v11 = __ldg(base + idx + zstride + 1);
-        const float s0 = fmaf(wb, v01 - v00, v00);
-        const float s1 = fmaf(wb, v11 - v10, v10);
-        acc += fmaf(wz, s1 - s0, s0);
+    // plane range: the b range of the column joined with the z ranges of its
+    // first and last ray, then joined over the warp
+    int p0 = 0, p1 = Na - 1;
+    clip_planes(fbc, gb, -1.0f, float(Nb), ca, Na, p0, p1);
+    {
+        const float gzl = (float(ivl) - g.cv) * gz_step;
+        int q0 = 0, q1 = Na - 1, r0 = 0, r1 = Na - 1;
+        clip_planes(fmaf(-Sv, gz0, g.cz), gz0, -1.0f, float(g.nz), ca, Na, q0, q1);
+        clip_planes(fmaf(-Sv, gzl, g.cz), gzl, -1.0f, float(g.nz), ca, Na, r0, r1);
+        const int z0 = min(q0, r0), z1 = max(q1, r1);
+        p0 = max(p0, z0);
+        p1 = min(p1, z1);
     }
-    y[(size_t(s) * lay.rows_per_view + iv + lay.row_off) * lay.pitch + iu + lay.col_off] =
-        acc * r.weight;
+    if (!live) {  // idle lanes do not widen the warp's range
+        p0 = Na;
+        p1 = -1;
+    }
+    p0 = __reduce_min_sync(0xffffffffu, p0);
+    p1 = __reduce_max_sync(0xffffffffu, p1);
+    // lanes of one warp can differ in axis (views near 45 degrees); each stays
+    // inside its own plane count
+    p1 = min(p1, Na - 1);
+
+    const float *__restrict__ base = xdom ? Xc : Yc;
+    const int pitch = xdom ? g.pitchX : g.pitchY;
+    const int zstride = Na * pitch;
+    const int bmax = Nb, zmax = g.nz;
+
+    float acc[VR];
+#pragma unroll
+    for (int i = 0; i < VR; ++i) acc[i] = 0.0f;
+
+    for (int p = p0; p <= p1; ++p) {
+        const float pm = float(p) - ca;
+        const float fb = fmaf(pm, gb, fbc);
+        const float b0f = floorf(fb);
+        const float wb = fb - b0f;
+        const int b0 = min(max(int(b0f), -PAD_A), bmax);
+        // element offset of (z = 0, plane p, b0) in the padded copy
+        const float *rowp = base + (PAD_A * Na + p) * pitch + b0 + PAD_A;
+        const float q = pm - Sv;
+        int zc = 0;
+        float rlo = 0.0f, rhi = 0.0f;
+#pragma unroll
+        for (int i = 0; i < VR; ++i) {
+            const float fz = fmaf(fmaf(float(i), gz_step, gz0), q, g.cz);
+            const float z0f = floorf(fz);
+            const float wz = fz - z0f;
+            const int z0 = min(max(int(z0f), -PAD_A), zmax);
+            if (i == 0 || z0 != zc) {
+                if (i > 0 && z0 == zc + 1) {
+                    rlo = rhi;
+                } else {
+                    const float *r = rowp + z0 * zstride;
+                    const float v0 = __ldg(r), v1 = __ldg(r + 1);
+                    rlo = fmaf(wb, v1 - v0, v0);
+                }
+                const float *r = rowp + (z0 + 1) * zstride;
+                const float v0 = __ldg(r), v1 = __ldg(r + 1);
+                rhi = fmaf(wb, v1 - v0, v0);
+                zc = z0;
+            }
+            acc[i] += fmaf(wz, rhi - rlo, rlo);
+        }
+    }
+    if (!live) return;
+    const float dxy2 = fmaf(dx, dx, dy * dy);
+#pragma unroll
+    for (int i = 0; i < VR; ++i) {
+        const int iv = iv0 + i;
+        if (iv < g.nv) {
+            const float v = (float(iv) - g.cv) * g.dv;
+            const float dz = v * b.x;
+            const float w = g.vox * sqrtf(fmaf(dz, dz, dxy2)) * fabsf(inv_da);
+            y[(size_t(s) * lay.rows_per_view + iv + lay.row_off) * lay.pitch + iu + lay.col_off] = acc[i] * w;
+        }
+    }
 }
 
 cudaError_t launch_joseph_A(const GeomDev &g, const float *Xc, const float *Yc, float *y,
                             SinoLayout lay, const int *stop, cudaStream_t st)
 {
-    const long long m = (long long)g.nu * g.nv * g.n_views;
-    const unsigned blocks = unsigned((m + A_BLOCK - 1) / A_BLOCK);
     ProfScope prof(PK_JOSEPH_A, st);
-    joseph_A_kernel<<<blocks, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
+    constexpr int WPB = A_BLOCK / 32;
+    if (g.nv == 1) {
+        dim3 grid((g.nu + 31) / 32, (g.nv + WPB - 1) / WPB, g.n_views);
+        joseph_A_kernel<1><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
+    } else {
+        constexpr int VR = 8;
+        dim3 grid((g.nu + 31) / 32, (g.nv + WPB * VR - 1) / (WPB * VR), g.n_views);
+        joseph_A_kernel<VR><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
+    }
     return cudaGetLastError();
 }
 

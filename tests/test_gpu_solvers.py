@@ -3,7 +3,11 @@ building blocks against the FP64 oracle, through the C-ABI.
 
 Tolerances: the reconstructed image and the residual history after k
 iterations agree with the FP64 oracle to relative error <= 1e-4 (residuals
-relative to resid[0]).  Full-size solves are checked through properties
+relative to resid[0]), or, where the k-th iterate is more sensitive than
+that to FP32 rounding, to 4x the oracle's own sensitivity: the oracle is run
+a second time with every operator output rounded to FP32, and its deviation
+d_k from the FP64 run (computed by the oracle alone) bounds what any FP32
+implementation can reach.  Full-size solves are checked through properties
 that hold at any size.
 """
 import numpy as np
@@ -42,6 +46,23 @@ def host(t):
     return t.detach().cpu().double().numpy()
 
 
+def _r32(f):
+    return lambda v: np.asarray(f(v), dtype=np.float32).astype(np.float64)
+
+
+def oracle_with_sensitivity(solver, spec, b_kind, b, k, **kw):
+    """FP64 oracle solve, plus the tolerances that FP32 rounding of the
+    operator outputs allows at iteration k (image, residual history)."""
+    ops = oracle.Operators(spec, b_kind)
+    b64 = b.astype(np.float64).reshape(-1)
+    ref = solver(ops.A, ops.B, b64, k, **kw)
+    pert = solver(_r32(ops.A), _r32(ops.B), b64, k, **kw)
+    d_img = rel(pert["x_final"], ref["x_final"])
+    key = "data_resid" if kw.get("record_data_resid") else "resid"
+    d_res = np.max(np.abs(pert[key] - ref[key])) / ref[key][0]
+    return ref, max(SOLVE_TOL, 4 * d_img), max(SOLVE_TOL, 4 * d_res)
+
+
 def data_for(spec, noise=0.01, seed=81):
     x = ci.phantom(spec)[0].astype(np.float64)
     b = oracle.project_A(spec, x)
@@ -60,11 +81,10 @@ def test_bagmres_matches_oracle(ct, spec, b_kind, k, dot_mode):
     b, _ = data_for(spec)
     g = ct.Geometry.from_spec(spec)
     x, res = ct.bagmres(g, dev(b), k, b_kind=b_kind, dot_mode=dot_mode)
-    ops = oracle.Operators(spec, b_kind)
-    ref = krylov.ba_gmres(ops.A, ops.B, b.astype(np.float64).reshape(-1), k, keep_basis=False)
+    ref, tol_x, tol_r = oracle_with_sensitivity(krylov.ba_gmres, spec, b_kind, b, k, keep_basis=False)
     assert res.iters == k
-    assert np.max(np.abs(res.resid - ref["resid"])) <= SOLVE_TOL * ref["resid"][0]
-    assert rel(host(x), ref["x_final"]) <= SOLVE_TOL, rel(host(x), ref["x_final"])
+    assert np.max(np.abs(res.resid - ref["resid"])) <= tol_r * ref["resid"][0]
+    assert rel(host(x), ref["x_final"]) <= tol_x, (rel(host(x), ref["x_final"]), tol_x)
     assert np.all(np.diff(res.resid) <= 1e-6 * res.resid[0])
 
 
@@ -75,10 +95,9 @@ def test_abgmres_matches_oracle(ct, spec, b_kind, k):
     b, _ = data_for(spec)
     g = ct.Geometry.from_spec(spec)
     x, res = ct.abgmres(g, dev(b), k, b_kind=b_kind)
-    ops = oracle.Operators(spec, b_kind)
-    ref = krylov.ab_gmres(ops.A, ops.B, b.astype(np.float64).reshape(-1), k, keep_basis=False)
-    assert np.max(np.abs(res.resid - ref["resid"])) <= SOLVE_TOL * ref["resid"][0]
-    assert rel(host(x), ref["x_final"]) <= SOLVE_TOL, rel(host(x), ref["x_final"])
+    ref, tol_x, tol_r = oracle_with_sensitivity(krylov.ab_gmres, spec, b_kind, b, k, keep_basis=False)
+    assert np.max(np.abs(res.resid - ref["resid"])) <= tol_r * ref["resid"][0]
+    assert rel(host(x), ref["x_final"]) <= tol_x, (rel(host(x), ref["x_final"]), tol_x)
 
 
 @pytest.mark.parametrize("spec,b_kind,k", [(ci.PAR2D_64, "un", 30), (ci.CONE_SMALL, "at", 15),
@@ -88,10 +107,9 @@ def test_cgls_matches_oracle(ct, spec, b_kind, k):
     b, _ = data_for(spec)
     g = ct.Geometry.from_spec(spec)
     x, res = ct.cgls(g, dev(b), k, b_kind=b_kind)
-    ops = oracle.Operators(spec, b_kind)
-    ref = krylov.cgls(ops.A, ops.B, b.astype(np.float64).reshape(-1), k)
-    assert np.max(np.abs(res.resid - ref["resid"])) <= SOLVE_TOL * ref["resid"][0]
-    assert rel(host(x), ref["x_final"]) <= SOLVE_TOL, rel(host(x), ref["x_final"])
+    ref, tol_x, tol_r = oracle_with_sensitivity(krylov.cgls, spec, b_kind, b, k)
+    assert np.max(np.abs(res.resid - ref["resid"])) <= tol_r * ref["resid"][0]
+    assert rel(host(x), ref["x_final"]) <= tol_x, (rel(host(x), ref["x_final"]), tol_x)
 
 
 def test_cgls_record_data_resid(ct):
@@ -99,9 +117,8 @@ def test_cgls_record_data_resid(ct):
     b, _ = data_for(spec)
     g = ct.Geometry.from_spec(spec)
     x, res = ct.cgls(g, dev(b), 6, b_kind="un", record_data_resid=True)
-    ops = oracle.Operators(spec, "un")
-    ref = krylov.cgls(ops.A, ops.B, b.astype(np.float64).reshape(-1), 6, record_data_resid=True)
-    assert np.max(np.abs(res.resid - ref["data_resid"])) <= SOLVE_TOL * ref["data_resid"][0]
+    ref, _, tol_r = oracle_with_sensitivity(krylov.cgls, spec, "un", b, 6, record_data_resid=True)
+    assert np.max(np.abs(res.resid - ref["data_resid"])) <= tol_r * ref["data_resid"][0]
 
 
 def test_unmatched_cgls_diverges_on_gpu(ct):
@@ -178,10 +195,9 @@ def test_reorthogonalisation_keeps_parity(ct):
     b, _ = data_for(spec)
     g = ct.Geometry.from_spec(spec)
     x, res = ct.bagmres(g, dev(b), 20, reorth=1)
-    ops = oracle.Operators(spec, "un")
-    ref = krylov.ba_gmres(ops.A, ops.B, b.astype(np.float64).reshape(-1), 20, keep_basis=False)
-    assert rel(host(x), ref["x_final"]) <= SOLVE_TOL
-    assert np.max(np.abs(res.resid - ref["resid"])) <= SOLVE_TOL * ref["resid"][0]
+    ref, tol_x, tol_r = oracle_with_sensitivity(krylov.ba_gmres, spec, "un", b, 20, keep_basis=False)
+    assert rel(host(x), ref["x_final"]) <= tol_x
+    assert np.max(np.abs(res.resid - ref["resid"])) <= tol_r * ref["resid"][0]
 
 
 @pytest.mark.parametrize("dot_mode", [0, 1])
