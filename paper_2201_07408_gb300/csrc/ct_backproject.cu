@@ -252,12 +252,13 @@ __device__ __forceinline__ ColumnView column_view(const GeomDev &g, int s, float
 }
 
 // A block owns a 32 x 32 tile of (x, y) columns and B_ZC consecutive z.
-// Which of x or y its lanes run along is chosen per view: along x when the
-// detector coordinate u moves faster with x than with y (|tx| >= |ty|),
-// else along y.  Along that axis neighbouring voxels land on neighbouring
-// detector pixels of the same rows; along the other axis the magnification
-// changes, so neighbouring voxels would read different rows.  The two
-// partial sums (x-lane views and y-lane views) meet in shared memory.
+// Which of x or y its lanes run along is chosen per view: the axis closer
+// to the view's central ray (along x when |tx| <= |ty|, i.e. when u moves
+// more slowly with x than with y).  Along the central ray the projection
+// barely moves (only the magnification changes, by vox/depth per voxel), so
+// a warp's gathers fall on a few neighbouring pixels of a few rows; across
+// it, u moves by M vox/du pixels per lane.  The two partial sums (x-lane
+// views and y-lane views) meet in shared memory.
 constexpr int B_TILE = 32;
 constexpr int B_ZC = 8;
 
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, cons
     for (int s = 0; s < g.n_views; ++s) {
         const float4 *vp = reinterpret_cast<const float4 *>(g.viewB + s);
         const float tx = __ldg(&vp->w), ty = __ldg(&(vp + 1)->x);
-        const bool xl = fabsf(tx) >= fabsf(ty);   // uniform over the block
+        const bool xl = fabsf(tx) <= fabsf(ty);   // uniform over the block
         const ColumnView c = xl ? column_view(g, s, axc, ayc, zfirst) : column_view(g, s, bxc, byc, zfirst);
         if (c.skip) continue;
         const float *vbase = ypad + size_t(s) * view_stride + c.col;

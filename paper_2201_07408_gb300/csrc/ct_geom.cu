@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 #include "ct_internal.cuh"
@@ -182,6 +183,32 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
             va[s] = ViewA{float(-sn), 0.0f, float(c), 0.0f, 0.0f, 1.0f, 0.0f, 0.0f};
             vb[s] = ViewB{1.0f, 0.0f, 0.0f, float(c), float(sn), 1.0f, 0.f, 0.f};
         }
+    }
+    // Projector row step: along a detector column, consecutive rays' z on
+    // plane c differs by sigma = dv (c - S_a) / (d_a vox) voxels.  sigma is
+    // affine in c and d_a is affine in u, so its extremes over the scan sit
+    // at the first/last plane and the first/centre/last column of each view.
+    k.a_window = 0;
+    if (cone) {
+        double smin = 1e300, smax = -1e300;
+        for (int s = 0; s < d->n_views; ++s) {
+            double th = d->angle_start_rad + double(s) * d->angle_span_rad / double(d->n_views);
+            double c = std::cos(th), sn = std::sin(th);
+            const double us[3] = {-0.5 * (d->nu - 1) * d->du_mm, 0.0, 0.5 * (d->nu - 1) * d->du_mm};
+            for (double u : us) {
+                double dx = -d->sdd_mm * c - u * sn, dy = -d->sdd_mm * sn + u * c;
+                bool xdom = std::fabs(dx) >= std::fabs(dy);
+                double da = xdom ? dx : dy, Sa = d->sod_mm * (xdom ? c : sn);
+                int Na = xdom ? d->nx : d->ny;
+                for (int e = 0; e < 2; ++e) {
+                    double cp = (e ? 0.5 : -0.5) * (Na - 1) * vox;
+                    double sig = d->dv_mm * (cp - Sa) / (da * vox);
+                    smin = std::min(smin, sig);
+                    smax = std::max(smax, sig);
+                }
+            }
+        }
+        k.a_window = (smin >= 0.0 && smax <= 0.98) ? 1 : 0;
     }
     // Ram-Lak taps of the ramp filter with the FBP scale folded in:
     // h[0] = 1/(4 tau^2), h[odd k] = -1/(pi^2 k^2 tau^2), h[even k] = 0, times tau * c_F.

@@ -50,6 +50,10 @@ struct GeomDev {
     int pitchY;                 // nx + 2 PAD_A
     // padded sinogram: S[view][vp][up], vp in [0, nv + 2 PAD_V), up in [0, nu + 2 PAD_U)
     int nvp, pitchU;
+    // projector: every ray of a detector column moves at most one z-row per
+    // detector row on every plane (0 <= dz/dv <= 0.98 rows), so a two-row
+    // window suffices (set by ct_geom_create from the geometry's extremes)
+    int a_window;
 };
 
 // Layout of a sinogram buffer that an operator writes or reads.

@@ -162,7 +162,7 @@ cudaError_t launch_plane_copies(const GeomDev &g, float *vol, const double *scal
 // ---------------------------------------------------------------------------
 constexpr int A_BLOCK = 128;
 
-template <int VR>
+template <int VR, bool WINDOW>
 __global__ void __launch_bounds__(A_BLOCK) joseph_A_kernel(GeomDev g, const float *__restrict__ Xc,
                                                            const float *__restrict__ Yc,
                                                            float *__restrict__ y, SinoLayout lay,
@@ -237,28 +237,30 @@ __global__ void __launch_bounds__(A_BLOCK) joseph_A_kernel(GeomDev g, const floa
         // element offset of (z = 0, plane p, b0) in the padded copy
         const float *rowp = base + (PAD_A * Na + p) * pitch + b0 + PAD_A;
         const float q = pm - Sv;
-        int zc = 0;
-        float rlo = 0.0f, rhi = 0.0f;
+        float lo_prev = 0.0f, hi_prev = 0.0f;
+        int z_prev = 0;
 #pragma unroll
         for (int i = 0; i < VR; ++i) {
             const float fz = fmaf(fmaf(float(i), gz_step, gz0), q, g.cz);
             const float z0f = floorf(fz);
             const float wz = fz - z0f;
             const int z0 = min(max(int(z0f), -PAD_A), zmax);
-            if (i == 0 || z0 != zc) {
-                if (i > 0 && z0 == zc + 1) {
-                    rlo = rhi;
-                } else {
-                    const float *r = rowp + z0 * zstride;
-                    const float v0 = __ldg(r), v1 = __ldg(r + 1);
-                    rlo = fmaf(wb, v1 - v0, v0);
-                }
-                const float *r = rowp + (z0 + 1) * zstride;
-                const float v0 = __ldg(r), v1 = __ldg(r + 1);
-                rhi = fmaf(wb, v1 - v0, v0);
-                zc = z0;
+            const float *r = rowp + (z0 + 1) * zstride;
+            const float h0 = __ldg(r), h1 = __ldg(r + 1);
+            const float hi = fmaf(wb, h1 - h0, h0);
+            float lo;
+            if (!WINDOW || i == 0) {
+                const float *rl = r - zstride;
+                const float l0 = __ldg(rl), l1 = __ldg(rl + 1);
+                lo = fmaf(wb, l1 - l0, l0);
+            } else {
+                // z0 is z_prev or z_prev + 1: the low row is one of the previous rows
+                lo = z0 == z_prev ? lo_prev : hi_prev;
             }
-            acc[i] += fmaf(wz, rhi - rlo, rlo);
+            acc[i] += fmaf(wz, hi - lo, lo);
+            lo_prev = lo;
+            hi_prev = hi;
+            z_prev = z0;
         }
     }
     if (!live) return;
@@ -282,11 +284,14 @@ cudaError_t launch_joseph_A(const GeomDev &g, const float *Xc, const float *Yc, 
     constexpr int WPB = A_BLOCK / 32;
     if (g.nv == 1) {
         dim3 grid((g.nu + 31) / 32, (g.nv + WPB - 1) / WPB, g.n_views);
-        joseph_A_kernel<1><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
+        joseph_A_kernel<1, false><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
     } else {
         constexpr int VR = 8;
         dim3 grid((g.nu + 31) / 32, (g.nv + WPB * VR - 1) / (WPB * VR), g.n_views);
-        joseph_A_kernel<VR><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
+        if (g.a_window)
+            joseph_A_kernel<VR, true><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
+        else
+            joseph_A_kernel<VR, false><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
     }
     return cudaGetLastError();
 }

@@ -4,11 +4,14 @@ building blocks against the FP64 oracle, through the C-ABI.
 Tolerances: the reconstructed image and the residual history after k
 iterations agree with the FP64 oracle to relative error <= 1e-4 (residuals
 relative to resid[0]), or, where the k-th iterate is more sensitive than
-that to FP32 rounding, to 4x the oracle's own sensitivity: the oracle is run
-a second time with every operator output rounded to FP32, and its deviation
-d_k from the FP64 run (computed by the oracle alone) bounds what any FP32
-implementation can reach.  Full-size solves are checked through properties
-that hold at any size.
+that to FP32 operator error, to 3x the oracle's own sensitivity: the oracle
+is run a second time with every operator output perturbed by a seeded
+relative error of 1e-6 (the class of the FP32 operators' error, which the
+operator tests bound by 1e-5 and measure at ~3e-7 to 7e-7), and its
+deviation d_k from the unperturbed run (computed by the oracle alone) is
+what an FP32 implementation can be expected to reach at iteration k; near a
+stagnation of GMRES on noisy data d_k reaches 1e-2.  Full-size solves are
+checked through properties that hold at any size.
 """
 import numpy as np
 import pytest
@@ -46,21 +49,28 @@ def host(t):
     return t.detach().cpu().double().numpy()
 
 
-def _r32(f):
-    return lambda v: np.asarray(f(v), dtype=np.float32).astype(np.float64)
+OP_EPS = 1e-6
+
+
+def _perturbed(f, rng):
+    def g(v):
+        y = np.asarray(f(v), dtype=np.float64)
+        return y * (1.0 + OP_EPS * rng.standard_normal(y.shape))
+    return g
 
 
 def oracle_with_sensitivity(solver, spec, b_kind, b, k, **kw):
-    """FP64 oracle solve, plus the tolerances that FP32 rounding of the
-    operator outputs allows at iteration k (image, residual history)."""
+    """FP64 oracle solve, plus the tolerances that an FP32-class operator
+    error allows at iteration k (image, residual history)."""
     ops = oracle.Operators(spec, b_kind)
     b64 = b.astype(np.float64).reshape(-1)
     ref = solver(ops.A, ops.B, b64, k, **kw)
-    pert = solver(_r32(ops.A), _r32(ops.B), b64, k, **kw)
+    rng = np.random.default_rng(97)
+    pert = solver(_perturbed(ops.A, rng), _perturbed(ops.B, rng), b64, k, **kw)
     d_img = rel(pert["x_final"], ref["x_final"])
     key = "data_resid" if kw.get("record_data_resid") else "resid"
     d_res = np.max(np.abs(pert[key] - ref[key])) / ref[key][0]
-    return ref, max(SOLVE_TOL, 4 * d_img), max(SOLVE_TOL, 4 * d_res)
+    return ref, max(SOLVE_TOL, 3 * d_img), max(SOLVE_TOL, 3 * d_res)
 
 
 def data_for(spec, noise=0.01, seed=81):
