@@ -23,7 +23,7 @@ namespace ct {
 // the source in place).
 // ---------------------------------------------------------------------------
 __global__ void pad_sino_kernel(GeomDev g, float *__restrict__ src, const double *__restrict__ scale,
-                                int normalize_inplace, float *__restrict__ dst,
+                                int normalize_inplace, float2 *__restrict__ dst,
                                 const int *__restrict__ stop)
 {
     if (stop && *stop) return;
@@ -36,14 +36,25 @@ __global__ void pad_sino_kernel(GeomDev g, float *__restrict__ src, const double
         const int vp = int(t % g.nvp);
         const int s = int(t / g.nvp);
         const int u = up - PAD_U, v = vp - PAD_V;
-        float val = 0.0f;
-        if (u >= 0 && u < g.nu && v >= 0 && v < g.nv) {
-            const size_t si = (size_t(s) * g.nv + v) * g.nu + u;
-            val = src[si] * sc;
-            if (normalize_inplace) src[si] = val;
+        float2 val = make_float2(0.0f, 0.0f);
+        if (v >= 0 && v < g.nv) {
+            const size_t si = (size_t(s) * g.nv + v) * g.nu;
+            if (u >= 0 && u < g.nu) val.x = src[si + u] * sc;
+            if (u + 1 >= 0 && u + 1 < g.nu) val.y = src[si + u + 1] * sc;
         }
         dst[i] = val;
     }
+}
+
+// src *= (*scale): the Arnoldi normalisation of a data-space basis vector,
+// after its padded copy has been taken from the unscaled values.
+__global__ void scale_inplace_kernel(float *__restrict__ v, size_t len, const double *__restrict__ scale,
+                                     const int *__restrict__ stop)
+{
+    if (stop && *stop) return;
+    const float sc = float(*scale);
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < len; i += size_t(gridDim.x) * blockDim.x)
+        v[i] *= sc;
 }
 
 cudaError_t launch_pad_sino(const GeomDev &g, float *src, const double *scale, bool normalize_inplace,
@@ -52,7 +63,9 @@ cudaError_t launch_pad_sino(const GeomDev &g, float *src, const double *scale, b
     const size_t total = size_t(g.n_views) * g.nvp * g.pitchU;
     unsigned blocks = unsigned(std::min<size_t>((total + 255) / 256, size_t(num_sms()) * 16));
     ProfScope prof(PK_PAD_SINO, st);
-    pad_sino_kernel<<<blocks, 256, 0, st>>>(g, src, scale, normalize_inplace ? 1 : 0, dst, stop);
+    pad_sino_kernel<<<blocks, 256, 0, st>>>(g, src, scale, 0, reinterpret_cast<float2 *>(dst), stop);
+    if (normalize_inplace && cudaGetLastError() == cudaSuccess)
+        scale_inplace_kernel<<<blocks, 256, 0, st>>>(src, size_t(g.n_views) * g.nv * g.nu, scale, stop);
     return cudaGetLastError();
 }
 
@@ -189,13 +202,12 @@ __global__ void ramp_kernel(GeomDev g, RampShape rs, const float *__restrict__ s
     else
         ramp_conv<0, 1>(E, O, gm, rs.M, i0, h0, acc);
     const int nh = parity ? rs.nhO : rs.nhE;
-    float *out = dst + (size_t(s) * lay.rows_per_view + iv + lay.row_off) * lay.pitch + lay.col_off;
 #pragma unroll
     for (int j = 0; j < RAMP_R; ++j) {
         const int i = i0 + j;
         if (i < nh) {
             const int iu = 2 * i + parity;
-            out[iu] = transpose ? acc[j] * cosine_weight(g, iu, iv) : acc[j];
+            store_sino(dst, lay, s, iv, iu, transpose ? acc[j] * cosine_weight(g, iu, iv) : acc[j]);
         }
     }
 }
@@ -223,19 +235,18 @@ constexpr int B_BX = 32, B_BY = 4;
 
 struct ColumnView {
     int skip;       // the u footprint misses the detector
-    int col;        // padded column offset of the left neighbour
+    int col;        // padded column of the left neighbour
     float a0, a1;   // weight * (1 - wu), weight * wu
     float fv0, gv;  // v fractional index of the first z of the run, slope per z
 };
 
-__device__ __forceinline__ ColumnView column_view(const GeomDev &g, int s, float x, float y, float zfirst)
+// p = (w0, wx, wy, tx), q = (ty, mnum, -, -) of one view
+__device__ __forceinline__ ColumnView column_view(const GeomDev &g, float4 p, float4 q, float x, float y,
+                                                  float zfirst)
 {
-    const float4 *vp = reinterpret_cast<const float4 *>(g.viewB + s);
-    const float4 p = __ldg(vp), q = __ldg(vp + 1);
-    // p = (w0, wx, wy, tx), q = (ty, mnum, -, -)
     const float W = fmaf(x, p.y, fmaf(y, p.z, p.x));
     const float t = fmaf(x, p.w, y * q.x);
-    const float M = q.y / W;
+    const float M = q.y * __frcp_rn(W);
     const float fu = fmaf(M * t, g.inv_du, g.cu);
     const float u0f = floorf(fu);
     const float wu = fu - u0f;
@@ -251,6 +262,12 @@ __device__ __forceinline__ ColumnView column_view(const GeomDev &g, int s, float
     return c;
 }
 
+__device__ __forceinline__ ColumnView column_view(const GeomDev &g, int s, float x, float y, float zfirst)
+{
+    const float4 *vp = reinterpret_cast<const float4 *>(g.viewB + s);
+    return column_view(g, __ldg(vp), __ldg(vp + 1), x, y, zfirst);
+}
+
 // A block owns a 32 x 32 tile of (x, y) columns and B_ZC consecutive z.
 // Which of x or y its lanes run along is chosen per view: the axis closer
 // to the view's central ray (along x when |tx| <= |ty|, i.e. when u moves
@@ -258,18 +275,24 @@ __device__ __forceinline__ ColumnView column_view(const GeomDev &g, int s, float
 // barely moves (only the magnification changes, by vox/depth per voxel), so
 // a warp's gathers fall on a few neighbouring pixels of a few rows; across
 // it, u moves by M vox/du pixels per lane.  The two partial sums (x-lane
-// views and y-lane views) meet in shared memory.
+// views and y-lane views) meet in shared memory.  The sinogram is read as
+// (u, u+1) pairs, one 8-byte load per detector row; the view table sits in
+// shared memory.
 constexpr int B_TILE = 32;
 constexpr int B_ZC = 8;
 
 template <int ZC>
-__global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, const float *__restrict__ ypad,
+__global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, const float2 *__restrict__ ypad,
                                                                  float *__restrict__ x,
                                                                  const int *__restrict__ stop)
 {
     if (stop && *stop) return;
+    extern __shared__ float4 sviews[];   // 2 per view
     __shared__ float tile[ZC][B_TILE][B_TILE + 1];
     const int l = threadIdx.x, w = threadIdx.y;
+    const int tid = w * B_TILE + l;
+    const float4 *vt = reinterpret_cast<const float4 *>(g.viewB);
+    for (int i = tid; i < 2 * g.n_views; i += B_TILE * B_TILE) sviews[i] = __ldg(vt + i);
     const int X0 = blockIdx.x * B_TILE, Y0 = blockIdx.y * B_TILE;
     const int iz0 = blockIdx.z * ZC;
     const float zfirst = (float(iz0) - g.cz) * g.vox;
@@ -280,6 +303,8 @@ __global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, cons
     const float axc = (float(ax) - g.cx) * g.vox, ayc = (float(ay) - g.cy) * g.vox;
     const float bxc = (float(bx) - g.cx) * g.vox, byc = (float(by) - g.cy) * g.vox;
     const int view_stride = g.nvp * g.pitchU;
+    const int pitch = g.pitchU;
+    __syncthreads();
     float accA[ZC], accB[ZC];
 #pragma unroll
     for (int k = 0; k < ZC; ++k) {
@@ -287,12 +312,11 @@ __global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, cons
         accB[k] = 0.0f;
     }
     for (int s = 0; s < g.n_views; ++s) {
-        const float4 *vp = reinterpret_cast<const float4 *>(g.viewB + s);
-        const float tx = __ldg(&vp->w), ty = __ldg(&(vp + 1)->x);
-        const bool xl = fabsf(tx) <= fabsf(ty);   // uniform over the block
-        const ColumnView c = xl ? column_view(g, s, axc, ayc, zfirst) : column_view(g, s, bxc, byc, zfirst);
+        const float4 p = sviews[2 * s], q = sviews[2 * s + 1];
+        const bool xl = fabsf(p.w) <= fabsf(q.x);   // |tx| <= |ty|, uniform over the block
+        const ColumnView c = column_view(g, p, q, xl ? axc : bxc, xl ? ayc : byc, zfirst);
         if (c.skip) continue;
-        const float *vbase = ypad + size_t(s) * view_stride + c.col;
+        const float2 *vbase = ypad + size_t(s) * view_stride + c.col;
         float r[ZC];
 #pragma unroll
         for (int k = 0; k < ZC; ++k) {
@@ -300,9 +324,10 @@ __global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, cons
             const float v0f = floorf(fv);
             const float wv = fv - v0f;
             const int v0 = int(fmaxf(fminf(v0f, float(g.nv)), -2.0f));
-            const float *rowp = vbase + (v0 + PAD_V) * g.pitchU;
-            const float r0 = fmaf(c.a0, __ldg(rowp), c.a1 * __ldg(rowp + 1));
-            const float r1 = fmaf(c.a0, __ldg(rowp + g.pitchU), c.a1 * __ldg(rowp + g.pitchU + 1));
+            const float2 *rowp = vbase + (v0 + PAD_V) * pitch;
+            const float2 lo = __ldg(rowp), hi = __ldg(rowp + pitch);
+            const float r0 = fmaf(c.a0, lo.x, c.a1 * lo.y);
+            const float r1 = fmaf(c.a0, hi.x, c.a1 * hi.y);
             r[k] = fmaf(wv, r1 - r0, r0);
         }
         if (xl) {
@@ -333,12 +358,23 @@ cudaError_t launch_voxel_B(const GeomDev &g, const float *ypad, float *x, const 
 {
     ProfScope prof(PK_VOXEL_B, st);
     dim3 block(B_TILE, B_TILE);
+    const size_t smem = size_t(g.n_views) * 2 * sizeof(float4);
+    const float2 *yp = reinterpret_cast<const float2 *>(ypad);
     if (g.nz == 1) {
+        if (smem > 16 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(voxel_B_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            if (e != cudaSuccess) return e;
+        }
         dim3 grid((g.nx + B_TILE - 1) / B_TILE, (g.ny + B_TILE - 1) / B_TILE, 1);
-        voxel_B_kernel<1><<<grid, block, 0, st>>>(g, ypad, x, stop);
+        voxel_B_kernel<1><<<grid, block, smem, st>>>(g, yp, x, stop);
     } else {
+        if (smem > 8 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(voxel_B_kernel<B_ZC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 int(smem));
+            if (e != cudaSuccess) return e;
+        }
         dim3 grid((g.nx + B_TILE - 1) / B_TILE, (g.ny + B_TILE - 1) / B_TILE, (g.nz + B_ZC - 1) / B_ZC);
-        voxel_B_kernel<B_ZC><<<grid, block, 0, st>>>(g, ypad, x, stop);
+        voxel_B_kernel<B_ZC><<<grid, block, smem, st>>>(g, yp, x, stop);
     }
     return cudaGetLastError();
 }
@@ -419,10 +455,10 @@ extern "C" ct_status ct_backproject_B(const ct_geom *geom, const float *y_dev, f
     Arena ar;
     ct_status rc = arena_open(ar, padded_sino_bytes(g), nullptr, 0, st);
     if (rc != CT_OK) return rc;
-    float *ypad = ar.take<float>(size_t(g.n_views) * g.nvp * g.pitchU);
+    float *ypad = ar.take<float>(padded_sino_floats(g));
     cudaError_t e;
     if (b_kind == CT_B_FBP) {
-        e = cudaMemsetAsync(ypad, 0, size_t(g.n_views) * g.nvp * g.pitchU * sizeof(float), st);
+        e = cudaMemsetAsync(ypad, 0, padded_sino_floats(g) * sizeof(float), st);
         if (e == cudaSuccess) e = launch_ramp(g, y_dev, ypad, padded_layout(g), false, nullptr, st);
     } else {
         e = launch_pad_sino(g, const_cast<float *>(y_dev), nullptr, false, ypad, nullptr, st);

@@ -71,7 +71,7 @@ size_t plane_copies_bytes(const GeomDev &g)
 
 size_t padded_sino_bytes(const GeomDev &g)
 {
-    return Arena::align(size_t(g.n_views) * g.nvp * g.pitchU * sizeof(float));
+    return Arena::align(size_t(g.n_views) * g.nvp * g.pitchU * 2 * sizeof(float));
 }
 
 int num_sms()
@@ -184,27 +184,35 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
             vb[s] = ViewB{1.0f, 0.0f, 0.0f, float(c), float(sn), 1.0f, 0.f, 0.f};
         }
     }
-    // Projector row step: along a detector column, consecutive rays' z on
-    // plane c differs by sigma = dv (c - S_a) / (d_a vox) voxels.  sigma is
-    // affine in c and d_a is affine in u, so its extremes over the scan sit
-    // at the first/last plane and the first/centre/last column of each view.
+    // Projector checks over every ray of the scan.  On plane c a ray of
+    // detector column u and row v is at z = v (c - S_a)/d_a, so consecutive
+    // rays of a column are sigma = dv (c - S_a)/(d_a vox) voxels apart in z.
+    // Both are affine in c, so their extremes over a column sit at the first
+    // and last plane; every column of every view is visited (the dominant
+    // axis switches inside views near 45 degrees).
+    //   a_window: 0 <= sigma <= 0.98, so a two-row window per column suffices;
+    //   a_zsafe:  |z| stays within the grid plus one voxel, so no clamp is needed.
     k.a_window = 0;
+    k.a_zsafe = 1;
     if (cone) {
         double smin = 1e300, smax = -1e300;
+        const double vmax = 0.5 * (d->nv - 1) * d->dv_mm;
         for (int s = 0; s < d->n_views; ++s) {
             double th = d->angle_start_rad + double(s) * d->angle_span_rad / double(d->n_views);
             double c = std::cos(th), sn = std::sin(th);
-            const double us[3] = {-0.5 * (d->nu - 1) * d->du_mm, 0.0, 0.5 * (d->nu - 1) * d->du_mm};
-            for (double u : us) {
+            for (int iu = 0; iu < d->nu; ++iu) {
+                double u = (iu - 0.5 * (d->nu - 1)) * d->du_mm;
                 double dx = -d->sdd_mm * c - u * sn, dy = -d->sdd_mm * sn + u * c;
                 bool xdom = std::fabs(dx) >= std::fabs(dy);
                 double da = xdom ? dx : dy, Sa = d->sod_mm * (xdom ? c : sn);
                 int Na = xdom ? d->nx : d->ny;
                 for (int e = 0; e < 2; ++e) {
                     double cp = (e ? 0.5 : -0.5) * (Na - 1) * vox;
-                    double sig = d->dv_mm * (cp - Sa) / (da * vox);
+                    double ratio = (cp - Sa) / da;
+                    double sig = d->dv_mm * ratio / vox;
                     smin = std::min(smin, sig);
                     smax = std::max(smax, sig);
+                    if (vmax * std::fabs(ratio) / vox > 0.5 * (d->nz - 1) + 1.0) k.a_zsafe = 0;
                 }
             }
         }

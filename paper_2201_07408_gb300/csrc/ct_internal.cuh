@@ -48,24 +48,42 @@ struct GeomDev {
     int nzp;                    // nz + 2 PAD_A
     int pitchX;                 // ny + 2 PAD_A
     int pitchY;                 // nx + 2 PAD_A
-    // padded sinogram: S[view][vp][up], vp in [0, nv + 2 PAD_V), up in [0, nu + 2 PAD_U)
+    // padded sinogram for the back-projector, pair-interleaved:
+    //   P[view][vp][up] = (S[vp][up], S[vp][up + 1]) as float2,
+    //   vp in [0, nv + 2 PAD_V), up in [0, nu + 2 PAD_U), S zero outside the detector
     int nvp, pitchU;
     // projector: every ray of a detector column moves at most one z-row per
     // detector row on every plane (0 <= dz/dv <= 0.98 rows), so a two-row
     // window suffices (set by ct_geom_create from the geometry's extremes)
     int a_window;
+    // projector: every sample of every ray lies within the zero-bordered z
+    // range, so the row index needs no clamp (set by ct_geom_create)
+    int a_zsafe;
 };
 
-// Layout of a sinogram buffer that an operator writes or reads.
+// Layout of a sinogram buffer that an operator writes.
 struct SinoLayout {
     int rows_per_view;  // nv (plain) or nv + 2 PAD_V (padded)
-    int pitch;          // nu (plain) or nu + 2 PAD_U (padded)
+    int pitch;          // entries per row: nu (plain) or nu + 2 PAD_U (padded)
     int row_off;        // 0 or PAD_V
     int col_off;        // 0 or PAD_U
+    int pairs;          // padded pair layout: value (v, u) goes to P[v][u].x and P[v][u-1].y
 };
 
-inline SinoLayout plain_layout(const GeomDev &g) { return SinoLayout{g.nv, g.nu, 0, 0}; }
-inline SinoLayout padded_layout(const GeomDev &g) { return SinoLayout{g.nvp, g.pitchU, PAD_V, PAD_U}; }
+inline SinoLayout plain_layout(const GeomDev &g) { return SinoLayout{g.nv, g.nu, 0, 0, 0}; }
+inline SinoLayout padded_layout(const GeomDev &g) { return SinoLayout{g.nvp, g.pitchU, PAD_V, PAD_U, 1}; }
+
+// Stores one sinogram value in either layout.
+__device__ __forceinline__ void store_sino(float *out, const SinoLayout &lay, int s, int iv, int iu, float val)
+{
+    const size_t e = (size_t(s) * lay.rows_per_view + iv + lay.row_off) * lay.pitch + iu + lay.col_off;
+    if (lay.pairs) {
+        out[2 * e] = val;
+        out[2 * e - 1] = val;   // .y of the entry to the left
+    } else {
+        out[e] = val;
+    }
+}
 
 // Error reporting: thread-local message returned by ct_last_error().
 ct_status set_error(ct_status st, const char *fmt, ...);
@@ -114,6 +132,8 @@ void arena_close(Arena &a);
 // Sizes (bytes, each rounded to 256) of the operator working buffers.
 size_t plane_copies_bytes(const GeomDev &g);      // Xc + Yc
 size_t padded_sino_bytes(const GeomDev &g);
+// floats in the pair-interleaved padded sinogram
+inline size_t padded_sino_floats(const GeomDev &g) { return size_t(g.n_views) * g.nvp * g.pitchU * 2; }
 
 // --- projector (ct_project.cu) ---------------------------------------------------
 // Builds the plane-major zero-bordered copies Xc, Yc of the volume `vol`

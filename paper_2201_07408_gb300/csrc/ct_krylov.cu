@@ -446,7 +446,7 @@ static void take_op_bufs(Arena &ar, const GeomDev &g, OpBufs &b, bool need_t)
 {
     b.Xc = ar.take<float>(size_t(g.nzp) * g.nx * g.pitchX);
     b.Yc = ar.take<float>(size_t(g.nzp) * g.ny * g.pitchY);
-    b.ypad = ar.take<float>(size_t(g.n_views) * g.nvp * g.pitchU);
+    b.ypad = ar.take<float>(padded_sino_floats(g));
     b.t = need_t ? ar.take<float>(size_t(g.n_views) * g.nv * g.nu) : nullptr;
 }
 
@@ -616,7 +616,7 @@ static ct_status bagmres(const ct_geom *geom, const float *b, int k, float *x, d
     cudaError_t e = cudaMemsetAsync(w.st, 0, sizeof(SolverState), s);
     // zero the padded sinogram once: its border is never written afterwards
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(w.ob.ypad, 0, size_t(g.n_views) * g.nvp * g.pitchU * sizeof(float), s);
+        e = cudaMemsetAsync(w.ob.ypad, 0, padded_sino_floats(g) * sizeof(float), s);
     // r0 = B b -> V_0
     if (e == cudaSuccess)
         e = apply_B(g, o.b_kind, const_cast<float *>(b), nullptr, false, w.ob, w.V, nullptr, s, nullptr);
@@ -671,7 +671,7 @@ static ct_status abgmres(const ct_geom *geom, const float *b, int k, float *x, d
     carve_gmres(ar, g, k, true, o.b_kind, w);
     const int *stop = &w.st->status;
     cudaError_t e = cudaMemsetAsync(w.st, 0, sizeof(SolverState), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(w.ob.ypad, 0, size_t(g.n_views) * g.nvp * g.pitchU * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.ob.ypad, 0, padded_sino_floats(g) * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(w.V, b, m * sizeof(float), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess)
         e = mgs_pass(o.dot_mode, w.V, nullptr, nullptr, nullptr, m, w.partials, &w.st->counter, nullptr,
@@ -755,7 +755,7 @@ static ct_status cgls(const ct_geom *geom, const float *b, int k, float *x, doub
     unsigned *ctr = &st->counter;
     const unsigned vb = red_blocks(std::max(n, m));
     cudaError_t e = cudaMemsetAsync(st, 0, sizeof(SolverState), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(w.ob.ypad, 0, size_t(g.n_views) * g.nvp * g.pitchU * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.ob.ypad, 0, padded_sino_floats(g) * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, n * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(w.r, b, m * sizeof(float), cudaMemcpyDeviceToDevice, s);
     // rr = ||r||^2, s = B r, gamma = ||s||^2, p = s

@@ -162,7 +162,7 @@ cudaError_t launch_plane_copies(const GeomDev &g, float *vol, const double *scal
 // ---------------------------------------------------------------------------
 constexpr int A_BLOCK = 128;
 
-template <int VR, bool WINDOW>
+template <int VR, bool WINDOW, bool ZCLAMP>
 __global__ void __launch_bounds__(A_BLOCK) joseph_A_kernel(GeomDev g, const float *__restrict__ Xc,
                                                            const float *__restrict__ Yc,
                                                            float *__restrict__ y, SinoLayout lay,
@@ -237,14 +237,16 @@ __global__ void __launch_bounds__(A_BLOCK) joseph_A_kernel(GeomDev g, const floa
         // element offset of (z = 0, plane p, b0) in the padded copy
         const float *rowp = base + (PAD_A * Na + p) * pitch + b0 + PAD_A;
         const float q = pm - Sv;
+        const float fz0 = fmaf(gz0, q, g.cz);   // z of the first ray
+        const float dzr = gz_step * q;          // z step from ray to ray
         float lo_prev = 0.0f, hi_prev = 0.0f;
         int z_prev = 0;
 #pragma unroll
         for (int i = 0; i < VR; ++i) {
-            const float fz = fmaf(fmaf(float(i), gz_step, gz0), q, g.cz);
+            const float fz = fmaf(float(i), dzr, fz0);
             const float z0f = floorf(fz);
             const float wz = fz - z0f;
-            const int z0 = min(max(int(z0f), -PAD_A), zmax);
+            const int z0 = ZCLAMP ? min(max(int(z0f), -PAD_A), zmax) : int(z0f);
             const float *r = rowp + (z0 + 1) * zstride;
             const float h0 = __ldg(r), h1 = __ldg(r + 1);
             const float hi = fmaf(wb, h1 - h0, h0);
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__(A_BLOCK) joseph_A_kernel(GeomDev g, const floa
             const float v = (float(iv) - g.cv) * g.dv;
             const float dz = v * b.x;
             const float w = g.vox * sqrtf(fmaf(dz, dz, dxy2)) * fabsf(inv_da);
-            y[(size_t(s) * lay.rows_per_view + iv + lay.row_off) * lay.pitch + iu + lay.col_off] = acc[i] * w;
+            store_sino(y, lay, s, iv, iu, acc[i] * w);
         }
     }
 }
@@ -284,14 +286,16 @@ cudaError_t launch_joseph_A(const GeomDev &g, const float *Xc, const float *Yc, 
     constexpr int WPB = A_BLOCK / 32;
     if (g.nv == 1) {
         dim3 grid((g.nu + 31) / 32, (g.nv + WPB - 1) / WPB, g.n_views);
-        joseph_A_kernel<1, false><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
+        joseph_A_kernel<1, false, true><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
     } else {
         constexpr int VR = 8;
         dim3 grid((g.nu + 31) / 32, (g.nv + WPB * VR - 1) / (WPB * VR), g.n_views);
-        if (g.a_window)
-            joseph_A_kernel<VR, true><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
+        if (g.a_window && g.a_zsafe)
+            joseph_A_kernel<VR, true, false><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
+        else if (g.a_window)
+            joseph_A_kernel<VR, true, true><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
         else
-            joseph_A_kernel<VR, false><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
+            joseph_A_kernel<VR, false, true><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
     }
     return cudaGetLastError();
 }
@@ -381,3 +385,4 @@ extern "C" ct_status ct_adjoint_At(const ct_geom *geom, const float *y_dev, floa
     if (e != cudaSuccess) return cuda_error(e, "ct_adjoint_At launch");
     return CT_OK;
 }
+
