@@ -204,6 +204,34 @@ CT_API ct_status ct_mgs_sweep(const float *V_dev, size_t ldv, int j, size_t len,
 CT_API ct_status ct_basis_combine(const float *V_dev, size_t ldv, int k, size_t len,
                            const double *y_dev, float *x_dev, void *stream);
 
+/* Size in bytes of the fixed device scratch of ct_project_A_noalloc. */
+#define CT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* y = A x exactly as ct_project_A, for callers that cannot allocate device
+ * memory while they run: a TensorRT plugin inside enqueue(), a framework
+ * that has reserved the whole device memory for its own pool, or a
+ * real-time loop that must not pay for, or fail on, an allocation.  The
+ * paper has no counterpart; this is a deployment variant of the projector.
+ *   - Scratch: the projector's two zero-bordered plane-major copies of x
+ *     live in a CT_NOALLOC_SCRATCH_BYTES (32 MiB) array that the library
+ *     defines in device memory; every GPU that loads the library holds it
+ *     until the process exits.  No cudaMalloc, cudaFree or other allocating
+ *     call is made.
+ *   - Limit: volumes whose copies need more than the array, about 155^3
+ *     voxels for a cubic grid, are refused with CT_EINVAL and a message
+ *     giving the bytes needed.
+ *   - Set-up: the first call on a device looks up the array's device
+ *     address (cudaGetSymbolAddress) with that device current; make that
+ *     first call before any stream capture.  The geometry's device must be
+ *     the current device.
+ *   - Sharing: all calls use the same array.  Calls that can overlap on the
+ *     GPU (other streams, other host threads) race on it; order them on one
+ *     stream.  Each call rewrites all of the scratch it reads, so nothing
+ *     carries over from the previous call.
+ * Arguments and layouts as ct_project_A. */
+CT_API ct_status ct_project_A_noalloc(const ct_geom *geom, const float *x_dev, float *y_dev,
+                                      void *stream);
+
 /* Per-kernel timing (no counterpart in the paper; instrumentation for
  * measurement).  ct_profile_enable(1) makes every kernel launch of the
  * library record a CUDA event pair on its stream; ct_profile_read waits for

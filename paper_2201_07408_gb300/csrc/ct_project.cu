@@ -21,6 +21,8 @@
 // (S x d)_z rather than from S + t d, which in FP32 would cancel two terms of
 // the size of the source distance; (S x d)_z = sod*u exactly for this
 // geometry, so the intercept keeps full relative precision.
+#include <mutex>
+
 #include "ct_internal.cuh"
 
 namespace ct {
@@ -386,3 +388,54 @@ extern "C" ct_status ct_adjoint_At(const ct_geom *geom, const float *y_dev, floa
     return CT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Projector without allocation: the plane copies live in a fixed device
+// array instead of stream-ordered scratch (see ct_project_A_noalloc in ct.h).
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoallocFloats = CT_NOALLOC_SCRATCH_BYTES / sizeof(float);
+__device__ __align__(256) float g_noalloc_scratch[kNoallocFloats];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float *g_noalloc_addr[kNoallocMaxDevices] = {};  // device address of the array, per device
+}  // namespace
+
+extern "C" ct_status ct_project_A_noalloc(const ct_geom *geom, const float *x_dev, float *y_dev,
+                                          void *stream)
+{
+    if (!geom || !x_dev || !y_dev) return set_error(CT_EINVAL, "ct_project_A_noalloc: NULL argument");
+    const GeomDev &g = geom->g;
+    const size_t xc_bytes = Arena::align(size_t(g.nzp) * g.nx * g.pitchX * sizeof(float));
+    const size_t yc_bytes = Arena::align(size_t(g.nzp) * g.ny * g.pitchY * sizeof(float));
+    if (xc_bytes + yc_bytes > size_t(CT_NOALLOC_SCRATCH_BYTES))
+        return set_error(CT_EINVAL,
+                         "ct_project_A_noalloc: this volume needs %zu bytes of projector scratch, more than "
+                         "the %zu-byte fixed scratch; use ct_project_A",
+                         xc_bytes + yc_bytes, size_t(CT_NOALLOC_SCRATCH_BYTES));
+    int dev = -1;
+    CT_CUDA(cudaGetDevice(&dev));
+    if (dev != geom->device)
+        return set_error(CT_EINVAL, "ct_project_A_noalloc: the geometry lives on device %d but device %d is current",
+                         geom->device, dev);
+    if (dev < 0 || dev >= kNoallocMaxDevices)
+        return set_error(CT_EINVAL, "ct_project_A_noalloc: device index %d is out of range", dev);
+    float *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(projector scratch)");
+            g_noalloc_addr[dev] = static_cast<float *>(p);
+        }
+        base = g_noalloc_addr[dev];
+    }
+    float *Xc = base;
+    float *Yc = base + xc_bytes / sizeof(float);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_plane_copies(g, const_cast<float *>(x_dev), nullptr, false, Xc, Yc, nullptr, st);
+    if (e == cudaSuccess) e = launch_joseph_A(g, Xc, Yc, y_dev, plain_layout(g), nullptr, st);
+    if (e != cudaSuccess) return cuda_error(e, "ct_project_A_noalloc launch");
+    return CT_OK;
+}

@@ -56,6 +56,7 @@ SIGNATURES = {
     "ct_geom_m": (_sz, [_vp]),
     "ct_project_A": (_i, [_vp, _vp, _vp, _vp]),
     "ct_backproject_B": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "ct_project_A_noalloc": (_i, [_vp, _vp, _vp, _vp]),
     "ct_adjoint_At": (_i, [_vp, _vp, _vp, _vp]),
     "ct_adjoint_Bt": (_i, [_vp, _vp, _vp, _i, _vp]),
     "ct_ramp_F": (_i, [_vp, _vp, _vp, _i, _vp]),
@@ -181,6 +182,14 @@ def ct_project_A(geom: Geometry, x, y, stream=None):
     d = geom.device
     _check("ct_project_A", lib().ct_project_A(geom.handle, _ptr(x, geom.n, "x", d), _ptr(y, geom.m, "y", d),
                                               _stream(stream, d)))
+
+
+def ct_project_A_noalloc(geom: Geometry, x, y, stream=None):
+    """y = A x without any device allocation (fixed 32 MiB library scratch);
+    see ct_project_A_noalloc in include/ct.h for the limit and sharing rules."""
+    d = geom.device
+    _check("ct_project_A_noalloc", lib().ct_project_A_noalloc(geom.handle, _ptr(x, geom.n, "x", d),
+                                                              _ptr(y, geom.m, "y", d), _stream(stream, d)))
 
 
 def ct_backproject_B(geom: Geometry, y, x, b_kind=CT_B_UN, stream=None):
