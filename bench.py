@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--workload", default=ci.CONE_256.name)
     ap.add_argument("--iters", type=int, default=K_ITERS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16"],
+                    help="storage of the working copies and the Krylov basis (arithmetic stays FP32)")
     ap.add_argument("--op", default=None, choices=["A", "B", "Bfbp", "F", "At", "Bt", "mgs"],
                     help="time one operator of the workload instead of the solve (profiling aid)")
     return ap.parse_args()
@@ -243,7 +245,7 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     spec = ci.WORKLOADS[args.workload]
-    g = ct.Geometry.from_spec(spec, device=dev)
+    g = ct.Geometry.from_spec(spec, device=dev, vol_dtype=args.storage, sino_dtype=args.storage)
     x_true = make_inputs(spec)
     x_true_d = torch.from_numpy(x_true).to(dev)
     p = ct.project_A(g, x_true_d)
@@ -347,6 +349,7 @@ def run_ours(args, world, rank, local):
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(elapsed_max / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "storage": args.storage,
             "data": "synthetic: 12 seeded ellipsoids, Poisson(1e5) -log data",
             "config": {"workload": spec.name, "voxels": list(spec.vol_shape), "views": spec.n_views,
                        "detector": [spec.nv, spec.nu], "b_kind": B_KIND, "iters_per_step": k,
@@ -386,7 +389,7 @@ def run_op(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     spec = ci.WORKLOADS[args.workload]
-    g = ct.Geometry.from_spec(spec, device=dev)
+    g = ct.Geometry.from_spec(spec, device=dev, vol_dtype=args.storage, sino_dtype=args.storage)
     x = torch.from_numpy(make_inputs(spec)).to(dev)
     y = ct.project_A(g, x)
     out_v = torch.empty(spec.vol_shape, device=dev)
@@ -420,7 +423,7 @@ def run_op(args):
     ct.profile_enable(False)
     prof = {k: v for k, v in ct.profile_read().items() if v[1]}
     ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"op": args.op, "workload": spec.name, "ms_per_call": round(ms, 4),
+    print(json.dumps({"op": args.op, "workload": spec.name, "storage": args.storage, "ms_per_call": round(ms, 4),
                       "kernels": {k: {"ms_per_launch": round(v[0] / v[1], 4), "launches": v[1]}
                                   for k, v in prof.items()},
                       "joseph_samples": spec.joseph_samples(), "voxel_view_samples": spec.voxel_view_samples()}),

@@ -72,7 +72,7 @@ typedef enum {
     CT_B_AT = 2    /* the exact transpose A^T (matched pair; CGLS reference) */
 } ct_b_kind;
 
-typedef enum { CT_SOLVER_BA = 0, CT_SOLVER_AB = 1, CT_SOLVER_CGLS = 2 } ct_solver;
+typedef enum { CT_SOLVER_BA = 0, CT_SOLVER_AB = 1, CT_SOLVER_CGLS = 2, CT_SOLVER_BA_VJP = 3 } ct_solver;
 
 typedef struct {
     int kind;                  /* ct_geom_kind */
@@ -84,8 +84,11 @@ typedef struct {
     int nu, nv;                /* detector pixels; 2D parallel beam needs nv = 1 */
     double du_mm, dv_mm;       /* pixel pitch */
     double sod_mm, sdd_mm;     /* source-axis and source-detector distances (cone only) */
-    int vol_dtype;             /* ct_dtype of basis/volume storage; CT_F32 */
-    int sino_dtype;            /* ct_dtype of sinogram storage; CT_F32 */
+    int vol_dtype;             /* storage of the projector's working copies of the volume and of
+                                  the BA-GMRES Krylov basis: CT_F32 or CT_BF16 */
+    int sino_dtype;            /* storage of the back-projector's working sinogram: CT_F32 or
+                                  CT_BF16.  Arithmetic is FP32 (FP64 for the least squares) and
+                                  caller buffers are FP32 whatever the storage. */
 } ct_geom_desc;
 
 typedef struct ct_geom ct_geom;
@@ -108,8 +111,8 @@ CT_API void ct_solve_opts_default(ct_solve_opts *opts);
 
 /* Creates a geometry handle on the current device: validates the
  * description (positive sizes, 2D needs nz = nv = 1, cone needs
- * sdd > sod > 0 and the volume inside the source circle, FP32 dtypes) and
- * uploads per-view tables.  The library owns the handle; free it with
+ * sdd > sod > 0 and the volume inside the source circle) and
+ * uploads per-view tables; storage dtypes CT_F32 or CT_BF16.  The library owns the handle; free it with
  * ct_geom_destroy.  Returns CT_EINVAL or CT_ECUDA on failure (*out = NULL). */
 CT_API ct_status ct_geom_create(const ct_geom_desc *desc, ct_geom **out);
 
@@ -184,6 +187,21 @@ CT_API ct_status ct_abgmres_solve(const ct_geom *geom, const float *b_dev, int k
 CT_API ct_status ct_cgls_solve(const ct_geom *geom, const float *b_dev, int k, float *x_out_dev,
                         double *resid_hist, const ct_solve_opts *opts, int *iters_done,
                         void *stream);
+
+/* Gradient through a converged BA-GMRES solve (Sec. II, Eq. 5):
+ * x = (BA)^{-1} B b, so for a scalar loss L(x) with gx = dL/dx,
+ * dL/db = B^T (BA)^{-T} gx = B^T z where (A^T B^T) z = gx.  z is found by k
+ * iterations of GMRES on A^T B^T from z0 = 0 (or fewer, with opts->tol),
+ * with a new image-space Krylov basis: the forward solve's basis is not
+ * needed, so it need not be kept.  Each iteration applies B^T (voxel
+ * splatting; F^T after it for CT_B_FBP) and A^T (ray scatter).
+ *   gx_dev: n floats; gb_dev: m floats (output, dL/db).
+ *   resid_hist: HOST k+1 doubles, ||gx - A^T B^T z_j|| (resid[0] = ||gx||).
+ *   opts->b_kind: CT_B_UN or CT_B_FBP (the B of the forward solve).
+ * Other arguments and return codes as ct_bagmres_solve. */
+CT_API ct_status ct_bagmres_vjp(const ct_geom *geom, const float *gx_dev, int k, float *gb_dev,
+                                double *resid_hist, const ct_solve_opts *opts, int *iters_done,
+                                void *stream);
 
 /* Device workspace in bytes that a solve with these arguments needs when
  * the caller supplies it through ct_solve_opts (solver: ct_solver). */

@@ -232,4 +232,18 @@ class Operators:
         return backproject_B(self.g, y, filtered=self.b_kind == "fbp").reshape(-1)
 
 
+class AdjointOperators:
+    """A^T and B^T of one geometry as flat-vector callables."""
+
+    def __init__(self, g, b_kind="un"):
+        self.g = g
+        self.b_kind = b_kind
+
+    def At(self, y):
+        return adjoint_At(self.g, y).reshape(-1)
+
+    def Bt(self, x):
+        return adjoint_Bt(self.g, x, filtered=self.b_kind == "fbp").reshape(-1)
+
+
 from . import krylov, analytic  # noqa: E402,F401

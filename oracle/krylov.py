@@ -163,3 +163,13 @@ def cgls(A, B, b, k, record_data_resid=False):
         xs.append(x.copy())
     return dict(x=xs, x_final=x, resid=np.array(resid),
                 data_resid=np.array(data) if record_data_resid else None)
+
+
+def ba_gmres_vjp(At, Bt, gx, k):
+    """Gradient through the converged BA-GMRES solution x = (BA)^{-1} B b:
+    dL/db = B^T z with (A^T B^T) z = gx (gx = dL/dx), z from k GMRES steps on
+    A^T B^T from zero.  Returns dict(gb, resid, iters)."""
+    gx = np.asarray(gx, dtype=np.float64).reshape(-1)
+    out = gmres_core(lambda v: At(Bt(v)), gx, k, keep_basis=False)
+    z = out["z"][-1] if out["z"] else np.zeros_like(gx)
+    return dict(gb=np.asarray(Bt(z)).reshape(-1), resid=out["resid"], iters=out["iters"], z=z)

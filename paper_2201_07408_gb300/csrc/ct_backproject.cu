@@ -22,9 +22,9 @@ namespace ct {
 // Plain -> padded sinogram copy (optionally scaled, optionally normalising
 // the source in place).
 // ---------------------------------------------------------------------------
-__global__ void pad_sino_kernel(GeomDev g, float *__restrict__ src, const double *__restrict__ scale,
-                                int normalize_inplace, float2 *__restrict__ dst,
-                                const int *__restrict__ stop)
+template <bool BF>
+__global__ void pad_sino_kernel(GeomDev g, const float *__restrict__ src, const double *__restrict__ scale,
+                                void *__restrict__ dst, const int *__restrict__ stop)
 {
     if (stop && *stop) return;
     const size_t total = size_t(g.n_views) * g.nvp * g.pitchU;
@@ -35,14 +35,19 @@ __global__ void pad_sino_kernel(GeomDev g, float *__restrict__ src, const double
         const size_t t = i / g.pitchU;
         const int vp = int(t % g.nvp);
         const int s = int(t / g.nvp);
-        const int u = up - PAD_U, v = vp - PAD_V;
-        float2 val = make_float2(0.0f, 0.0f);
-        if (v >= 0 && v < g.nv) {
-            const size_t si = (size_t(s) * g.nv + v) * g.nu;
-            if (u >= 0 && u < g.nu) val.x = src[si + u] * sc;
-            if (u + 1 >= 0 && u + 1 < g.nu) val.y = src[si + u + 1] * sc;
-        }
-        dst[i] = val;
+        const int u = up - PAD_U, v = vp - g.padv;
+        const float *view = src + size_t(s) * g.nv * g.nu;
+        const bool u0 = u >= 0 && u < g.nu, u1 = u + 1 >= 0 && u + 1 < g.nu;
+        const bool v0 = v >= 0 && v < g.nv, v1 = v + 1 >= 0 && v + 1 < g.nv;
+        float4 q;
+        q.x = (v0 && u0) ? view[size_t(v) * g.nu + u] * sc : 0.0f;
+        q.y = (v0 && u1) ? view[size_t(v) * g.nu + u + 1] * sc : 0.0f;
+        q.z = (v1 && u0) ? view[size_t(v + 1) * g.nu + u] * sc : 0.0f;
+        q.w = (v1 && u1) ? view[size_t(v + 1) * g.nu + u + 1] * sc : 0.0f;
+        if (BF)
+            static_cast<uint2 *>(dst)[i] = make_uint2(pack_bf16x2(q.x, q.y), pack_bf16x2(q.z, q.w));
+        else
+            static_cast<float4 *>(dst)[i] = q;
     }
 }
 
@@ -60,10 +65,13 @@ __global__ void scale_inplace_kernel(float *__restrict__ v, size_t len, const do
 cudaError_t launch_pad_sino(const GeomDev &g, float *src, const double *scale, bool normalize_inplace,
                             float *dst, const int *stop, cudaStream_t st)
 {
+    ProfScope prof(PK_PAD_SINO, st);
     const size_t total = size_t(g.n_views) * g.nvp * g.pitchU;
     unsigned blocks = unsigned(std::min<size_t>((total + 255) / 256, size_t(num_sms()) * 16));
-    ProfScope prof(PK_PAD_SINO, st);
-    pad_sino_kernel<<<blocks, 256, 0, st>>>(g, src, scale, 0, reinterpret_cast<float2 *>(dst), stop);
+    if (g.sino_bf16)
+        pad_sino_kernel<true><<<blocks, 256, 0, st>>>(g, src, scale, dst, stop);
+    else
+        pad_sino_kernel<false><<<blocks, 256, 0, st>>>(g, src, scale, dst, stop);
     if (normalize_inplace && cudaGetLastError() == cudaSuccess)
         scale_inplace_kernel<<<blocks, 256, 0, st>>>(src, size_t(g.n_views) * g.nv * g.nu, scale, stop);
     return cudaGetLastError();
@@ -76,21 +84,26 @@ cudaError_t launch_pad_sino(const GeomDev &g, float *src, const double *scale, b
 //   out[2i+1] = h0 O[i] + sum_m g[m] (E[i-m]   + E[i+m+1])
 // with E, O the even / odd samples of the (cosine-weighted) row and
 // g[m] = h[2m+1].  A thread computes RAMP_R consecutive outputs of one
-// parity with two register windows that slide by one sample per tap, so
-// each tap costs two shared-memory loads for 2*RAMP_R FADD/FFMA; RAMP_R is
-// odd so that the window loads of neighbouring threads fall in distinct
-// banks.  Rows sit in shared memory with zero margins, so no load is
-// bounds-tested.  F^T weights the output instead of the input.
+// parity for two detector rows at once: the two rows are interleaved in
+// shared memory (float2), so each tap costs two 8-byte shared loads and
+// RAMP_R packed FADD2/FFMA2 for 2*RAMP_R outputs.  The two register windows
+// slide by one sample per tap as ring buffers whose slot indices are
+// compile-time constants (the tap loop is unrolled by RAMP_R and the tap
+// count padded with zero taps), so sliding costs no moves.  RAMP_R is odd
+// so that the window loads of neighbouring threads fall in distinct banks.
+// Rows sit in shared memory with zero margins, so no load is bounds-tested.
+// F^T weights the output instead of the input.
 // ---------------------------------------------------------------------------
 constexpr int RAMP_R = 9;
 
 struct RampShape {
-    int M;       // taps g[0..M-1]
+    int M;       // taps g[0..M-1], M a multiple of RAMP_R (zero taps past nu/2)
+    int mpad;    // floats reserved for the taps: M rounded up to 4, so the float2 rows start 16-byte aligned
     int nhE, nhO;
     int off;     // index of sample 0 inside a half-row array
-    int len;     // length of one half-row array
-    int tpr;     // threads per row
-    int rows;    // rows per block
+    int len;     // length of one half-row array (float2 entries)
+    int tpr;     // threads per row pair
+    int pairs;   // row pairs per block
     int threads;
     size_t smem;
 };
@@ -98,15 +111,18 @@ struct RampShape {
 static RampShape ramp_shape(int nu)
 {
     RampShape r;
-    r.M = nu / 2;
+    const int mtaps = nu / 2;
+    r.M = ((mtaps + RAMP_R - 1) / RAMP_R) * RAMP_R;
+    if (r.M == 0) r.M = RAMP_R;
     r.nhE = (nu + 1) / 2;
     r.nhO = nu / 2;
     r.off = r.M + 1;
     r.len = r.off + r.nhE + RAMP_R + r.M + 2;
     r.tpr = (r.nhE + RAMP_R - 1) / RAMP_R + (r.nhO + RAMP_R - 1) / RAMP_R;
-    r.rows = r.tpr >= 256 ? 1 : 256 / r.tpr;
-    r.threads = ((r.tpr * r.rows + 31) / 32) * 32;
-    r.smem = sizeof(float) * (size_t(r.M) + size_t(r.rows) * 2 * r.len);
+    r.pairs = r.tpr >= 256 ? 1 : 256 / r.tpr;
+    r.threads = ((r.tpr * r.pairs + 31) / 32) * 32;
+    r.mpad = (r.M + 3) & ~3;
+    r.smem = sizeof(float) * size_t(r.mpad) + sizeof(float2) * size_t(r.pairs) * 2 * r.len;
     return r;
 }
 
@@ -118,45 +134,36 @@ __device__ __forceinline__ float cosine_weight(const GeomDev &g, int iu, int iv)
     return g.sdd / sqrtf(fmaf(g.sdd, g.sdd, fmaf(u, u, v * v)));
 }
 
-// acc[j] = h0 C[i0+j] + sum_m g[m] (L[i0+j-m-AL] + Rr[i0+j+m+AR]), L == Rr
+__device__ __forceinline__ int ring(int x) { return ((x % RAMP_R) + RAMP_R) % RAMP_R; }
+
+// acc[j] = h0 C[i0+j] + sum_m g[m] (L[i0+j-m-AL] + L[i0+j+m+AR]) for two rows at once
 template <int AL, int AR>
-__device__ __forceinline__ void ramp_conv(const float *__restrict__ L, const float *__restrict__ C,
+__device__ __forceinline__ void ramp_conv(const float2 *__restrict__ L, const float2 *__restrict__ C,
                                           const float *__restrict__ gm, int M, int i0, float h0,
-                                          float (&acc)[RAMP_R])
+                                          float2 (&acc)[RAMP_R])
 {
-    float Lw[RAMP_R], Rw[RAMP_R];
+    // ring slots: left element q = i0 + j - m - AL sits in slot ring(q - i0),
+    // right element q = i0 + j + m + AR in slot ring(q - i0)
+    float2 Lw[RAMP_R], Rw[RAMP_R];
 #pragma unroll
-    for (int j = 0; j < RAMP_R; ++j) {
-        Lw[j] = L[i0 + j + 1 - AL];
-        Rw[j] = L[i0 + j - 1 + AR];
-        acc[j] = h0 * C[i0 + j];
+    for (int j = 0; j < RAMP_R; ++j) {   // state before tap 0 (m = -1)
+        Lw[ring(j + 1 - AL)] = L[i0 + j + 1 - AL];
+        Rw[ring(j - 1 + AR)] = L[i0 + j - 1 + AR];
+        const float2 c = C[i0 + j];
+        acc[j] = make_float2(h0 * c.x, h0 * c.y);
     }
-    int m = 0;
-    for (; m + RAMP_R <= M; m += RAMP_R) {
+    for (int m0 = 0; m0 < M; m0 += RAMP_R) {
 #pragma unroll
         for (int t = 0; t < RAMP_R; ++t) {
-            const int mm = m + t;
+            const int m = m0 + t;
+            Lw[ring(-t - AL)] = L[i0 - m - AL];                 // enters at j = 0
+            Rw[ring(RAMP_R - 1 + t + AR)] = L[i0 + RAMP_R - 1 + m + AR];   // enters at j = R-1
+            const float gv = gm[m];
+            const float2 g2 = make_float2(gv, gv);
 #pragma unroll
-            for (int j = RAMP_R - 1; j > 0; --j) Lw[j] = Lw[j - 1];
-            Lw[0] = L[i0 - mm - AL];
-#pragma unroll
-            for (int j = 0; j < RAMP_R - 1; ++j) Rw[j] = Rw[j + 1];
-            Rw[RAMP_R - 1] = L[i0 + RAMP_R - 1 + mm + AR];
-            const float gv = gm[mm];
-#pragma unroll
-            for (int j = 0; j < RAMP_R; ++j) acc[j] = fmaf(gv, Lw[j] + Rw[j], acc[j]);
+            for (int j = 0; j < RAMP_R; ++j)
+                acc[j] = __ffma2_rn(g2, __fadd2_rn(Lw[ring(j - t - AL)], Rw[ring(j + t + AR)]), acc[j]);
         }
-    }
-    for (; m < M; ++m) {
-#pragma unroll
-        for (int j = RAMP_R - 1; j > 0; --j) Lw[j] = Lw[j - 1];
-        Lw[0] = L[i0 - m - AL];
-#pragma unroll
-        for (int j = 0; j < RAMP_R - 1; ++j) Rw[j] = Rw[j + 1];
-        Rw[RAMP_R - 1] = L[i0 + RAMP_R - 1 + m + AR];
-        const float gv = gm[m];
-#pragma unroll
-        for (int j = 0; j < RAMP_R; ++j) acc[j] = fmaf(gv, Lw[j] + Rw[j], acc[j]);
     }
 }
 
@@ -167,47 +174,51 @@ __global__ void ramp_kernel(GeomDev g, RampShape rs, const float *__restrict__ s
     extern __shared__ float sm[];
     const int nu = g.nu;
     const int nrows = g.n_views * g.nv;
-    float *gm = sm;                                   // taps g[m] = h[2m+1]
-    const int row_base = blockIdx.x * rs.rows;
-    for (int i = threadIdx.x; i < rs.M; i += blockDim.x) gm[i] = g.ramp_taps[2 * i + 1];
-    // half rows with zero margins
-    for (int i = threadIdx.x; i < rs.rows * 2 * rs.len; i += blockDim.x) sm[rs.M + i] = 0.0f;
+    float *gm = sm;                                                 // taps g[m] = h[2m+1]
+    float2 *half = reinterpret_cast<float2 *>(sm + rs.mpad);        // [pair][E | O][len]
+    const int row_base = blockIdx.x * rs.pairs * 2;
+    for (int i = threadIdx.x; i < rs.M; i += blockDim.x) gm[i] = 2 * i + 1 < nu ? g.ramp_taps[2 * i + 1] : 0.0f;
+    for (int i = threadIdx.x; i < rs.pairs * 2 * rs.len; i += blockDim.x) half[i] = make_float2(0.0f, 0.0f);
     __syncthreads();
-    for (int i = threadIdx.x; i < rs.rows * nu; i += blockDim.x) {
-        const int lr = i / nu, iu = i - lr * nu;
+    float *halff = reinterpret_cast<float *>(half);
+    for (int i = threadIdx.x; i < rs.pairs * 2 * nu; i += blockDim.x) {
+        const int lr = i / nu, iu = i - lr * nu;     // lr: row within the block
         const int r = row_base + lr;
         if (r >= nrows) continue;
         const int iv = r % g.nv;
         const float w = transpose ? 1.0f : cosine_weight(g, iu, iv);
-        float *E = sm + rs.M + size_t(lr) * 2 * rs.len + rs.off;
-        float *O = E + rs.len;
-        (iu & 1 ? O : E)[iu >> 1] = src[size_t(r) * nu + iu] * w;
+        const int pair = lr >> 1, comp = lr & 1;
+        const size_t e = (size_t(pair) * 2 + (iu & 1)) * rs.len + rs.off + (iu >> 1);
+        halff[2 * e + comp] = src[size_t(r) * nu + iu] * w;
     }
     __syncthreads();
-    const int lr = threadIdx.x / rs.tpr;
-    const int tile = threadIdx.x - lr * rs.tpr;
-    const int r = row_base + lr;
-    if (lr >= rs.rows || r >= nrows) return;
-    const int iv = r % g.nv;
-    const int s = r / g.nv;
-    const float *E = sm + rs.M + size_t(lr) * 2 * rs.len + rs.off;
-    const float *O = E + rs.len;
+    const int lp = threadIdx.x / rs.tpr;
+    const int tile = threadIdx.x - lp * rs.tpr;
+    const int r0 = row_base + 2 * lp;
+    if (lp >= rs.pairs || r0 >= nrows) return;
+    const float2 *E = half + size_t(lp) * 2 * rs.len + rs.off;
+    const float2 *O = E + rs.len;
     const int tilesE = (rs.nhE + RAMP_R - 1) / RAMP_R;
     const int parity = tile < tilesE ? 0 : 1;
     const int i0 = (parity ? tile - tilesE : tile) * RAMP_R;
     const float h0 = g.ramp_taps[0];
-    float acc[RAMP_R];
+    float2 acc[RAMP_R];
     if (parity == 0)
         ramp_conv<1, 0>(O, E, gm, rs.M, i0, h0, acc);
     else
         ramp_conv<0, 1>(E, O, gm, rs.M, i0, h0, acc);
     const int nh = parity ? rs.nhO : rs.nhE;
+    const bool second = r0 + 1 < nrows;
+    const int iv0 = r0 % g.nv, s0 = r0 / g.nv;
+    const int iv1 = (r0 + 1) % g.nv, s1 = (r0 + 1) / g.nv;
 #pragma unroll
     for (int j = 0; j < RAMP_R; ++j) {
         const int i = i0 + j;
         if (i < nh) {
             const int iu = 2 * i + parity;
-            store_sino(dst, lay, s, iv, iu, transpose ? acc[j] * cosine_weight(g, iu, iv) : acc[j]);
+            store_sino(dst, lay, s0, iv0, iu, transpose ? acc[j].x * cosine_weight(g, iu, iv0) : acc[j].x);
+            if (second)
+                store_sino(dst, lay, s1, iv1, iu, transpose ? acc[j].y * cosine_weight(g, iu, iv1) : acc[j].y);
         }
     }
 }
@@ -222,7 +233,7 @@ cudaError_t launch_ramp(const GeomDev &g, const float *src, float *dst, SinoLayo
         if (e != cudaSuccess) return e;
     }
     const int nrows = g.n_views * g.nv;
-    const unsigned blocks = unsigned((nrows + rs.rows - 1) / rs.rows);
+    const unsigned blocks = unsigned((nrows + 2 * rs.pairs - 1) / (2 * rs.pairs));
     ProfScope prof(PK_RAMP, st);
     ramp_kernel<<<blocks, rs.threads, rs.smem, st>>>(g, rs, src, dst, lay, transpose ? 1 : 0, stop);
     return cudaGetLastError();
@@ -246,7 +257,12 @@ __device__ __forceinline__ ColumnView column_view(const GeomDev &g, float4 p, fl
 {
     const float W = fmaf(x, p.y, fmaf(y, p.z, p.x));
     const float t = fmaf(x, p.w, y * q.x);
-    const float M = q.y * __frcp_rn(W);
+    // 1/W: hardware approximation refined by one Newton step (W is a depth of
+    // hundreds of mm, or 1 in 2D, never denormal)
+    float rw;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rw) : "f"(W));
+    rw = fmaf(rw, fmaf(-W, rw, 1.0f), rw);
+    const float M = q.y * rw;
     const float fu = fmaf(M * t, g.inv_du, g.cu);
     const float u0f = floorf(fu);
     const float wu = fu - u0f;
@@ -281,8 +297,19 @@ __device__ __forceinline__ ColumnView column_view(const GeomDev &g, int s, float
 constexpr int B_TILE = 32;
 constexpr int B_ZC = 8;
 
-template <int ZC>
-__global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, const float2 *__restrict__ ypad,
+// the four bilinear neighbours of one sinogram quad entry
+template <bool BF>
+__device__ __forceinline__ float4 load_quad(const void *base, size_t e)
+{
+    if (BF) {
+        const uint2 w = __ldg(static_cast<const uint2 *>(base) + e);
+        return make_float4(bf16_lo(w.x), bf16_hi(w.x), bf16_lo(w.y), bf16_hi(w.y));
+    }
+    return __ldg(static_cast<const float4 *>(base) + e);
+}
+
+template <int ZC, bool BF>
+__global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, const void *__restrict__ ypad,
                                                                  float *__restrict__ x,
                                                                  const int *__restrict__ stop)
 {
@@ -316,18 +343,16 @@ __global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, cons
         const bool xl = fabsf(p.w) <= fabsf(q.x);   // |tx| <= |ty|, uniform over the block
         const ColumnView c = column_view(g, p, q, xl ? axc : bxc, xl ? ayc : byc, zfirst);
         if (c.skip) continue;
-        const float2 *vbase = ypad + size_t(s) * view_stride + c.col;
+        const size_t vbase = size_t(s) * view_stride + c.col;
         float r[ZC];
 #pragma unroll
         for (int k = 0; k < ZC; ++k) {
             const float fv = fmaf(float(k), c.gv, c.fv0);
             const float v0f = floorf(fv);
             const float wv = fv - v0f;
-            const int v0 = int(fmaxf(fminf(v0f, float(g.nv)), -2.0f));
-            const float2 *rowp = vbase + (v0 + PAD_V) * pitch;
-            const float2 lo = __ldg(rowp), hi = __ldg(rowp + pitch);
-            const float r0 = fmaf(c.a0, lo.x, c.a1 * lo.y);
-            const float r1 = fmaf(c.a0, hi.x, c.a1 * hi.y);
+            const float4 nb = load_quad<BF>(ypad, vbase + size_t((int(v0f) + g.padv) * pitch));
+            const float r0 = fmaf(c.a0, nb.x, c.a1 * nb.y);
+            const float r1 = fmaf(c.a0, nb.z, c.a1 * nb.w);
             r[k] = fmaf(wv, r1 - r0, r0);
         }
         if (xl) {
@@ -354,29 +379,29 @@ __global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, cons
     }
 }
 
+template <int ZC, bool BF>
+static cudaError_t launch_voxel_B_t(const GeomDev &g, const float *ypad, float *x, const int *stop, cudaStream_t st)
+{
+    dim3 block(B_TILE, B_TILE);
+    const size_t smem = size_t(g.n_views) * 2 * sizeof(float4);
+    if (smem > 8 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(voxel_B_kernel<ZC, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(smem));
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((g.nx + B_TILE - 1) / B_TILE, (g.ny + B_TILE - 1) / B_TILE, (g.nz + ZC - 1) / ZC);
+    voxel_B_kernel<ZC, BF><<<grid, block, smem, st>>>(g, ypad, x, stop);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_voxel_B(const GeomDev &g, const float *ypad, float *x, const int *stop, cudaStream_t st)
 {
     ProfScope prof(PK_VOXEL_B, st);
-    dim3 block(B_TILE, B_TILE);
-    const size_t smem = size_t(g.n_views) * 2 * sizeof(float4);
-    const float2 *yp = reinterpret_cast<const float2 *>(ypad);
-    if (g.nz == 1) {
-        if (smem > 16 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(voxel_B_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-            if (e != cudaSuccess) return e;
-        }
-        dim3 grid((g.nx + B_TILE - 1) / B_TILE, (g.ny + B_TILE - 1) / B_TILE, 1);
-        voxel_B_kernel<1><<<grid, block, smem, st>>>(g, yp, x, stop);
-    } else {
-        if (smem > 8 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(voxel_B_kernel<B_ZC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 int(smem));
-            if (e != cudaSuccess) return e;
-        }
-        dim3 grid((g.nx + B_TILE - 1) / B_TILE, (g.ny + B_TILE - 1) / B_TILE, (g.nz + B_ZC - 1) / B_ZC);
-        voxel_B_kernel<B_ZC><<<grid, block, smem, st>>>(g, yp, x, stop);
-    }
-    return cudaGetLastError();
+    if (g.nz == 1)
+        return g.sino_bf16 ? launch_voxel_B_t<1, true>(g, ypad, x, stop, st)
+                           : launch_voxel_B_t<1, false>(g, ypad, x, stop, st);
+    return g.sino_bf16 ? launch_voxel_B_t<B_ZC, true>(g, ypad, x, stop, st)
+                       : launch_voxel_B_t<B_ZC, false>(g, ypad, x, stop, st);
 }
 
 // ---------------------------------------------------------------------------

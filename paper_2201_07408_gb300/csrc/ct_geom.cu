@@ -71,7 +71,7 @@ size_t plane_copies_bytes(const GeomDev &g)
 
 size_t padded_sino_bytes(const GeomDev &g)
 {
-    return Arena::align(size_t(g.n_views) * g.nvp * g.pitchU * 2 * sizeof(float));
+    return Arena::align(size_t(g.n_views) * g.nvp * g.pitchU * 4 * sizeof(float));
 }
 
 int num_sms()
@@ -122,8 +122,8 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         return set_error(CT_EINVAL, "voxel and pixel sizes must be positive");
     if (!std::isfinite(d->angle_start_rad) || !std::isfinite(d->angle_span_rad))
         return set_error(CT_EINVAL, "view angles must be finite");
-    if (d->vol_dtype != CT_F32 || d->sino_dtype != CT_F32)
-        return set_error(CT_EINVAL, "only CT_F32 storage is supported");
+    if ((d->vol_dtype != CT_F32 && d->vol_dtype != CT_BF16) || (d->sino_dtype != CT_F32 && d->sino_dtype != CT_BF16))
+        return set_error(CT_EINVAL, "storage dtypes must be CT_F32 or CT_BF16");
     if (d->kind == CT_PARALLEL_2D && (d->nz != 1 || d->nv != 1))
         return set_error(CT_EINVAL, "2D parallel beam needs nz = 1 and nv = 1");
     if (d->kind == CT_CONE_3D) {
@@ -133,13 +133,24 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         if (std::sqrt(hx * hx + hy * hy) >= d->sod_mm)
             return set_error(CT_EINVAL, "the volume must lie inside the source circle");
     }
-    // 32-bit indexing of rays, voxels and padded copies
+    // back-projector row margin: a voxel at height z projects to row
+    // cv + M z/dv with M <= sdd/(sod - r_max); pad so that the floor of that
+    // and the row above stay inside the zero-bordered buffer
+    int padv = PAD_V;
+    if (d->kind == CT_CONE_3D) {
+        const double vx = d->voxel_mm;
+        const double rmax = std::sqrt(std::pow(0.5 * (d->nx - 1) * vx, 2) + std::pow(0.5 * (d->ny - 1) * vx, 2));
+        const double mmax = d->sdd_mm / (d->sod_mm - rmax);
+        const double over = 0.5 * (d->nz - 1) * vx * mmax / d->dv_mm - 0.5 * (d->nv - 1);
+        padv = std::max(PAD_V, int(std::ceil(std::max(over, 0.0))) + PAD_V);
+    }
+    // 32-bit indexing of rays, voxels, padded copies and the padded sinogram
     const double lim = 2147483647.0;
     double nzp = d->nz + 2.0 * PAD_A;
     if (double(d->n_views) * d->nv * d->nu >= lim ||
         double(d->nx) * d->ny * d->nz >= lim ||
         nzp * d->nx * (d->ny + 2.0 * PAD_A) >= lim || nzp * d->ny * (d->nx + 2.0 * PAD_A) >= lim ||
-        double(d->n_views) * (d->nv + 2.0 * PAD_V) * (d->nu + 2.0 * PAD_U) >= lim)
+        double(d->n_views) * (d->nv + 2.0 * padv) * (d->nu + 2.0 * PAD_U) * 4.0 >= lim)
         return set_error(CT_EINVAL, "problem too large for 32-bit element indexing");
 
     ct_geom *g = new ct_geom();
@@ -165,7 +176,10 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     k.nzp = d->nz + 2 * PAD_A;
     k.pitchX = d->ny + 2 * PAD_A;
     k.pitchY = d->nx + 2 * PAD_A;
-    k.nvp = d->nv + 2 * PAD_V;
+    k.padv = padv;
+    k.vol_bf16 = d->vol_dtype == CT_BF16;
+    k.sino_bf16 = d->sino_dtype == CT_BF16;
+    k.nvp = d->nv + 2 * k.padv;
     k.pitchU = d->nu + 2 * PAD_U;
 
     // per-view tables (computed in double, stored in float)

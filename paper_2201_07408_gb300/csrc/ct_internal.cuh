@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libct.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -48,10 +49,13 @@ struct GeomDev {
     int nzp;                    // nz + 2 PAD_A
     int pitchX;                 // ny + 2 PAD_A
     int pitchY;                 // nx + 2 PAD_A
-    // padded sinogram for the back-projector, pair-interleaved:
-    //   P[view][vp][up] = (S[vp][up], S[vp][up + 1]) as float2,
-    //   vp in [0, nv + 2 PAD_V), up in [0, nu + 2 PAD_U), S zero outside the detector
-    int nvp, pitchU;
+    // padded sinogram for the back-projector, quad-interleaved: entry
+    //   Q[view][vp][up] = (S[v][u], S[v][u+1], S[v+1][u], S[v+1][u+1]) as float4,
+    //   v = vp - padv, u = up - PAD_U, vp in [0, nv + 2 padv), up in [0, nu + 2 PAD_U),
+    //   S zero outside the detector: the four bilinear neighbours of a sample in one load.
+    // padv (>= PAD_V) rows of zeros cover every voxel's projection, so the
+    // back-projector's row index needs no clamp.
+    int nvp, pitchU, padv;
     // projector: every ray of a detector column moves at most one z-row per
     // detector row on every plane (0 <= dz/dv <= 0.98 rows), so a two-row
     // window suffices (set by ct_geom_create from the geometry's extremes)
@@ -59,6 +63,11 @@ struct GeomDev {
     // projector: every sample of every ray lies within the zero-bordered z
     // range, so the row index needs no clamp (set by ct_geom_create)
     int a_zsafe;
+    // storage precision of the working copies (arithmetic is FP32 either way):
+    //   vol_bf16:  projector plane copies hold (b, b+1) bf16 pairs in 4 bytes,
+    //              and the BA-GMRES Krylov basis is bf16;
+    //   sino_bf16: the back-projector's quad sinogram holds 4 bf16 (8 bytes).
+    int vol_bf16, sino_bf16;
 };
 
 // Layout of a sinogram buffer that an operator writes.
@@ -67,19 +76,36 @@ struct SinoLayout {
     int pitch;          // entries per row: nu (plain) or nu + 2 PAD_U (padded)
     int row_off;        // 0 or PAD_V
     int col_off;        // 0 or PAD_U
-    int pairs;          // padded pair layout: value (v, u) goes to P[v][u].x and P[v][u-1].y
+    int quads;          // padded quad layout: value (v, u) goes to the four entries that hold it
+    int bf16;           // quad entries hold bf16 instead of float
 };
 
-inline SinoLayout plain_layout(const GeomDev &g) { return SinoLayout{g.nv, g.nu, 0, 0, 0}; }
-inline SinoLayout padded_layout(const GeomDev &g) { return SinoLayout{g.nvp, g.pitchU, PAD_V, PAD_U, 1}; }
+inline SinoLayout plain_layout(const GeomDev &g) { return SinoLayout{g.nv, g.nu, 0, 0, 0, 0}; }
+inline SinoLayout padded_layout(const GeomDev &g)
+{
+    return SinoLayout{g.nvp, g.pitchU, g.padv, PAD_U, 1, g.sino_bf16};
+}
 
 // Stores one sinogram value in either layout.
 __device__ __forceinline__ void store_sino(float *out, const SinoLayout &lay, int s, int iv, int iu, float val)
 {
     const size_t e = (size_t(s) * lay.rows_per_view + iv + lay.row_off) * lay.pitch + iu + lay.col_off;
-    if (lay.pairs) {
-        out[2 * e] = val;
-        out[2 * e - 1] = val;   // .y of the entry to the left
+    if (lay.quads) {
+        // (v, u) is .x of entry (v, u), .y of (v, u-1), .z of (v-1, u), .w of (v-1, u-1)
+        const size_t up = e - lay.pitch;
+        if (lay.bf16) {
+            __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(out);
+            const __nv_bfloat16 h = __float2bfloat16_rn(val);
+            o[4 * e] = h;
+            o[4 * (e - 1) + 1] = h;
+            o[4 * up + 2] = h;
+            o[4 * (up - 1) + 3] = h;
+        } else {
+            out[4 * e] = val;
+            out[4 * (e - 1) + 1] = val;
+            out[4 * up + 2] = val;
+            out[4 * (up - 1) + 3] = val;
+        }
     } else {
         out[e] = val;
     }
@@ -132,16 +158,28 @@ void arena_close(Arena &a);
 // Sizes (bytes, each rounded to 256) of the operator working buffers.
 size_t plane_copies_bytes(const GeomDev &g);      // Xc + Yc
 size_t padded_sino_bytes(const GeomDev &g);
-// floats in the pair-interleaved padded sinogram
-inline size_t padded_sino_floats(const GeomDev &g) { return size_t(g.n_views) * g.nvp * g.pitchU * 2; }
+// 4-byte words in the quad-interleaved padded sinogram (4 floats or 4 bf16 per entry)
+inline size_t padded_sino_floats(const GeomDev &g)
+{
+    return size_t(g.n_views) * g.nvp * g.pitchU * (g.sino_bf16 ? 2 : 4);
+}
+
+// bf16 <-> float helpers for the packed working copies
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);   // .x in the low half
+    return *reinterpret_cast<const uint32_t *>(&p);
+}
 
 // --- projector (ct_project.cu) ---------------------------------------------------
-// Builds the plane-major zero-bordered copies Xc, Yc of the volume `vol`
-// scaled by (*scale) when scale != nullptr; when `normalize_inplace` the
-// scaled volume is also written back to `vol` (Arnoldi normalisation).
-cudaError_t launch_plane_copies(const GeomDev &g, float *vol, const double *scale,
-                                bool normalize_inplace, float *Xc, float *Yc,
-                                const int *stop, cudaStream_t st);
+// Builds the plane-major zero-bordered copies Xc, Yc (float, or bf16 pairs
+// when g.vol_bf16) of the volume `vol` scaled by (*scale) when scale !=
+// nullptr; when `basis_out` is given the scaled volume is also stored there
+// (the Arnoldi normalisation), as float or, when g.vol_bf16, as bf16.
+cudaError_t launch_plane_copies(const GeomDev &g, const float *vol, const double *scale, void *basis_out,
+                                float *Xc, float *Yc, const int *stop, cudaStream_t st);
 // y = A x from the plane copies, written in `lay`.
 cudaError_t launch_joseph_A(const GeomDev &g, const float *Xc, const float *Yc, float *y,
                             SinoLayout lay, const int *stop, cudaStream_t st);

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(RED_BLOCK) mgs_pass_kernel(
         for (size_t i = tid; i < n4; i += nth) {
             float4 a = q4[i];
             if (vprev) {
-                const float4 p = __ldg(p4 + i);
+                const float4 p = __ldcs(p4 + i);   // basis vectors stream through L2 (evict first)
                 a.x = fmaf(-h, p.x, a.x);
                 a.y = fmaf(-h, p.y, a.y);
                 a.z = fmaf(-h, p.z, a.z);
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(RED_BLOCK) mgs_pass_kernel(
                 q4[i] = a;
             }
             if (vcur) {
-                const float4 c = __ldg(c4 + i);
+                const float4 c = __ldcs(c4 + i);
                 dot.add(a.x, c.x);
                 dot.add(a.y, c.y);
                 dot.add(a.z, c.z);
@@ -184,6 +184,68 @@ __global__ void __launch_bounds__(RED_BLOCK) mgs_pass_kernel(
     grid_finish(dot.value(), ss.value(), partials, counter, out_dot, out_sumsq);
 }
 
+// The same pass with a bf16 basis (FP32 work vector q): eight elements per
+// step, the basis read as 16-byte vectors.
+__device__ __forceinline__ void unpack8(const uint4 w, float (&o)[8])
+{
+    o[0] = bf16_lo(w.x); o[1] = bf16_hi(w.x); o[2] = bf16_lo(w.y); o[3] = bf16_hi(w.y);
+    o[4] = bf16_lo(w.z); o[5] = bf16_hi(w.z); o[6] = bf16_lo(w.w); o[7] = bf16_hi(w.w);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(RED_BLOCK) mgs_pass_bf16_kernel(
+    float *__restrict__ q, const __nv_bfloat16 *__restrict__ vprev, const double *__restrict__ hprev,
+    const __nv_bfloat16 *__restrict__ vcur, size_t len, int vec8, double *__restrict__ partials,
+    unsigned *__restrict__ counter, double *__restrict__ out_dot, double *__restrict__ out_sumsq,
+    const int *__restrict__ stop, const int *__restrict__ skip)
+{
+    if ((stop && *stop) || (skip && *skip)) return;
+    const float h = vprev ? float(*hprev) : 0.0f;
+    Acc<MODE> dot, ss;
+    const size_t tid = blockIdx.x * size_t(RED_BLOCK) + threadIdx.x;
+    const size_t nth = size_t(gridDim.x) * RED_BLOCK;
+    size_t start = 0;
+    if (vec8) {
+        const size_t n8 = len / 8;
+        float4 *q4 = reinterpret_cast<float4 *>(q);
+        const uint4 *p8 = reinterpret_cast<const uint4 *>(vprev);
+        const uint4 *c8 = reinterpret_cast<const uint4 *>(vcur);
+        for (size_t i = tid; i < n8; i += nth) {
+            const float4 lo = q4[2 * i], hi = q4[2 * i + 1];
+            float a[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+            if (vprev) {
+                float pv[8];
+                unpack8(__ldcs(p8 + i), pv);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) a[e] = fmaf(-h, pv[e], a[e]);
+                q4[2 * i] = make_float4(a[0], a[1], a[2], a[3]);
+                q4[2 * i + 1] = make_float4(a[4], a[5], a[6], a[7]);
+            }
+            if (vcur) {
+                float cv[8];
+                unpack8(__ldcs(c8 + i), cv);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) dot.add(a[e], cv[e]);
+            }
+            if (out_sumsq) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) ss.add(a[e], a[e]);
+            }
+        }
+        start = n8 * 8;
+    }
+    for (size_t i = start + tid; i < len; i += nth) {
+        float a = q[i];
+        if (vprev) {
+            a = fmaf(-h, __bfloat162float(vprev[i]), a);
+            q[i] = a;
+        }
+        if (vcur) dot.add(a, __bfloat162float(vcur[i]));
+        if (out_sumsq) ss.add(a, a);
+    }
+    grid_finish(dot.value(), ss.value(), partials, counter, out_dot, out_sumsq);
+}
+
 // sum (a - b)^2 -> *out (recomputed data residuals)
 __global__ void __launch_bounds__(RED_BLOCK) diff_sumsq_kernel(const float *__restrict__ a,
                                                                const float *__restrict__ b, size_t len,
@@ -205,11 +267,11 @@ __global__ void __launch_bounds__(RED_BLOCK) diff_sumsq_kernel(const float *__re
 static unsigned red_blocks(size_t len)
 {
     size_t want = (len / 4 + RED_BLOCK - 1) / RED_BLOCK;
-    size_t cap = size_t(num_sms()) * 4;
+    size_t cap = size_t(num_sms()) * 8;
     return unsigned(std::max<size_t>(1, std::min(want, cap)));
 }
 
-static size_t partials_count() { return size_t(num_sms()) * 4 * 2; }
+static size_t partials_count() { return size_t(num_sms()) * 8 * 2; }
 
 static cudaError_t mgs_pass(int mode, float *q, const float *vprev, const double *hprev,
                             const float *vcur, size_t len, double *partials, unsigned *counter,
@@ -227,6 +289,31 @@ static cudaError_t mgs_pass(int mode, float *q, const float *vprev, const double
     else
         mgs_pass_kernel<1><<<blocks, RED_BLOCK, 0, st>>>(q, vprev, hprev, vcur, len, vec4, partials,
                                                          counter, out_dot, out_sumsq, stop, skip);
+    return cudaGetLastError();
+}
+
+// MGS pass over a typed basis (float or bf16 vectors; q is always float).
+static cudaError_t mgs_pass_typed(int mode, bool vbf16, float *q, const void *vprev, const double *hprev,
+                                  const void *vcur, size_t len, double *partials, unsigned *counter,
+                                  double *out_dot, double *out_sumsq, const int *stop, const int *skip,
+                                  cudaStream_t st)
+{
+    if (!vbf16)
+        return mgs_pass(mode, q, static_cast<const float *>(vprev), hprev, static_cast<const float *>(vcur), len,
+                        partials, counter, out_dot, out_sumsq, stop, skip, st);
+    const int vec8 = (len % 8 == 0) && (reinterpret_cast<uintptr_t>(q) % 16 == 0) &&
+                     (!vprev || reinterpret_cast<uintptr_t>(vprev) % 16 == 0) &&
+                     (!vcur || reinterpret_cast<uintptr_t>(vcur) % 16 == 0);
+    const unsigned blocks = red_blocks(len);
+    ProfScope prof(PK_MGS, st);
+    const auto *p = static_cast<const __nv_bfloat16 *>(vprev);
+    const auto *c = static_cast<const __nv_bfloat16 *>(vcur);
+    if (mode == 0)
+        mgs_pass_bf16_kernel<0><<<blocks, RED_BLOCK, 0, st>>>(q, p, hprev, c, len, vec8, partials, counter, out_dot,
+                                                              out_sumsq, stop, skip);
+    else
+        mgs_pass_bf16_kernel<1><<<blocks, RED_BLOCK, 0, st>>>(q, p, hprev, c, len, vec8, partials, counter, out_dot,
+                                                              out_sumsq, stop, skip);
     return cudaGetLastError();
 }
 
@@ -326,7 +413,8 @@ __global__ void backsolve_kernel(const double *R, const double *g, double *y, co
 }
 
 // x = sum_{i < count} y_i V_i ; count = *count_ptr when given, else k
-__global__ void __launch_bounds__(RED_BLOCK) combine_kernel(const float *__restrict__ V, size_t ldv, int k,
+template <typename TB>
+__global__ void __launch_bounds__(RED_BLOCK) combine_kernel(const TB *__restrict__ V, size_t ldv, int k,
                                                             size_t len, const double *__restrict__ y,
                                                             const int *__restrict__ count_ptr,
                                                             float *__restrict__ x)
@@ -338,25 +426,32 @@ __global__ void __launch_bounds__(RED_BLOCK) combine_kernel(const float *__restr
     for (size_t e = blockIdx.x * size_t(RED_BLOCK) + threadIdx.x; e < len;
          e += size_t(gridDim.x) * RED_BLOCK) {
         float acc = 0.0f;
-        for (int i = 0; i < count; ++i) acc = fmaf(ys[i], __ldg(V + i * ldv + e), acc);
+        for (int i = 0; i < count; ++i) acc = fmaf(ys[i], float(V[i * ldv + e]), acc);
         x[e] = acc;
     }
 }
 
-static cudaError_t combine(const float *V, size_t ldv, int k, size_t len, const double *y,
-                           const int *count_ptr, float *x, cudaStream_t st)
+template <typename TB>
+static cudaError_t combine_t(const TB *V, size_t ldv, int k, size_t len, const double *y, const int *count_ptr,
+                             float *x, cudaStream_t st)
 {
     const size_t smem = std::max<size_t>(1, size_t(k)) * sizeof(float);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(combine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(combine_kernel<TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(std::min<size_t>(smem, 200 * 1024)));
         if (e != cudaSuccess) return e;
     }
     const unsigned blocks = unsigned(std::max<size_t>(1, std::min((len + RED_BLOCK - 1) / RED_BLOCK,
                                                                   size_t(num_sms()) * 8)));
     ProfScope prof(PK_COMBINE, st);
-    combine_kernel<<<blocks, RED_BLOCK, smem, st>>>(V, ldv, k, len, y, count_ptr, x);
+    combine_kernel<TB><<<blocks, RED_BLOCK, smem, st>>>(V, ldv, k, len, y, count_ptr, x);
     return cudaGetLastError();
+}
+
+static cudaError_t combine(const float *V, size_t ldv, int k, size_t len, const double *y, const int *count_ptr,
+                           float *x, cudaStream_t st)
+{
+    return combine_t<float>(V, ldv, k, len, y, count_ptr, x, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -498,13 +593,20 @@ static size_t round_ld(size_t len) { return (len + 63) & ~size_t(63); }
 // Carves the GMRES workspace; with a counting arena (base == nullptr) it
 // only adds up the size.
 struct GmresWs {
-    float *V = nullptr;
+    void *V = nullptr;      // k+1 basis vectors, float or (BA-GMRES with vol_bf16) bf16
+    bool vbf16 = false;
     size_t ldv = 0;
+    float *q = nullptr;     // BA-GMRES: FP32 work vector (new Krylov vector)
     OpBufs ob;
     float *tvol = nullptr;  // AB-GMRES: B v_j
     double *H = nullptr, *H2 = nullptr, *R = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr,
            *resid = nullptr, *y = nullptr, *partials = nullptr;
     SolverState *st = nullptr;
+    const void *vec(int i) const
+    {
+        return static_cast<const char *>(V) + size_t(i) * ldv * (vbf16 ? 2 : 4);
+    }
+    void *vec(int i) { return static_cast<char *>(V) + size_t(i) * ldv * (vbf16 ? 2 : 4); }
 };
 
 static bool carve_gmres(Arena &ar, const GeomDev &g, int k, bool ab, int b_kind, GmresWs &w)
@@ -513,7 +615,12 @@ static bool carve_gmres(Arena &ar, const GeomDev &g, int k, bool ab, int b_kind,
     const size_t m = size_t(g.n_views) * g.nv * g.nu;
     const size_t len = ab ? m : n;
     w.ldv = round_ld(len);
-    w.V = ar.take<float>(w.ldv * size_t(k + 1));
+    w.vbf16 = !ab && g.vol_bf16;
+    if (w.vbf16)
+        w.V = ar.take<__nv_bfloat16>(w.ldv * size_t(k + 1));
+    else
+        w.V = ar.take<float>(w.ldv * size_t(k + 1));
+    if (!ab) w.q = ar.take<float>(n);
     // BA needs a plain sinogram when B reads one (F or A^T); AB never does
     take_op_bufs(ar, g, w.ob, !ab && b_kind != CT_B_UN);
     if (ab) w.tvol = ar.take<float>(n);
@@ -541,22 +648,23 @@ static size_t gmres_bytes(const GeomDev &g, int k, bool ab, int b_kind)
     return ar.used;
 }
 
-// Enqueues the MGS sweep of iteration j (q = V_{j+1}) and its Givens step.
-static cudaError_t arnoldi_orthogonalise(GmresWs &w, int j, int k, size_t len, const ct_solve_opts &o,
+// Enqueues the MGS sweep of iteration j (the new vector q against
+// V_0..V_j) and its Givens step.
+static cudaError_t arnoldi_orthogonalise(GmresWs &w, float *q, int j, int k, size_t len, const ct_solve_opts &o,
                                          cudaStream_t s)
 {
     const int *stop = &w.st->status;
     unsigned *ctr = &w.st->counter;
-    float *q = w.V + size_t(j + 1) * w.ldv;
     double *hcol = w.H + size_t(j) * (k + 1);
     cudaError_t e = cudaSuccess;
     for (int i = 0; i <= j + 1 && e == cudaSuccess; ++i) {
-        const float *vprev = i > 0 ? w.V + size_t(i - 1) * w.ldv : nullptr;
+        const void *vprev = i > 0 ? w.vec(i - 1) : nullptr;
         const double *hprev = i > 0 ? hcol + (i - 1) : nullptr;
-        const float *vcur = i <= j ? w.V + size_t(i) * w.ldv : nullptr;
+        const void *vcur = i <= j ? w.vec(i) : nullptr;
         double *odot = i <= j ? hcol + i : nullptr;
         double *oss = i == 0 ? &w.st->ref_sumsq : (i == j + 1 ? &w.st->sumsq : nullptr);
-        e = mgs_pass(o.dot_mode, q, vprev, hprev, vcur, len, w.partials, ctr, odot, oss, stop, nullptr, s);
+        e = mgs_pass_typed(o.dot_mode, w.vbf16, q, vprev, hprev, vcur, len, w.partials, ctr, odot, oss, stop,
+                           nullptr, s);
     }
     if (e != cudaSuccess) return e;
     const double *H2 = nullptr;
@@ -564,12 +672,13 @@ static cudaError_t arnoldi_orthogonalise(GmresWs &w, int j, int k, size_t len, c
         { ProfScope prof(PK_SMALL, s); reorth_decide_kernel<<<1, 1, 0, s>>>(w.st); }
         const int *skip = &w.st->reorth_skip;
         for (int i = 0; i <= j + 1 && e == cudaSuccess; ++i) {
-            const float *vprev = i > 0 ? w.V + size_t(i - 1) * w.ldv : nullptr;
+            const void *vprev = i > 0 ? w.vec(i - 1) : nullptr;
             const double *hprev = i > 0 ? w.H2 + (i - 1) : nullptr;
-            const float *vcur = i <= j ? w.V + size_t(i) * w.ldv : nullptr;
+            const void *vcur = i <= j ? w.vec(i) : nullptr;
             double *odot = i <= j ? w.H2 + i : nullptr;
             double *oss = i == j + 1 ? &w.st->sumsq : nullptr;
-            e = mgs_pass(o.dot_mode, q, vprev, hprev, vcur, len, w.partials, ctr, odot, oss, stop, skip, s);
+            e = mgs_pass_typed(o.dot_mode, w.vbf16, q, vprev, hprev, vcur, len, w.partials, ctr, odot, oss, stop,
+                               skip, s);
         }
         if (e != cudaSuccess) return e;
         H2 = w.H2;
@@ -617,36 +726,37 @@ static ct_status bagmres(const ct_geom *geom, const float *b, int k, float *x, d
     // zero the padded sinogram once: its border is never written afterwards
     if (e == cudaSuccess)
         e = cudaMemsetAsync(w.ob.ypad, 0, padded_sino_floats(g) * sizeof(float), s);
-    // r0 = B b -> V_0
+    // r0 = B b -> q; its norm starts the residual history
     if (e == cudaSuccess)
-        e = apply_B(g, o.b_kind, const_cast<float *>(b), nullptr, false, w.ob, w.V, nullptr, s, nullptr);
+        e = apply_B(g, o.b_kind, const_cast<float *>(b), nullptr, false, w.ob, w.q, nullptr, s, nullptr);
     if (e == cudaSuccess)
-        e = mgs_pass(o.dot_mode, w.V, nullptr, nullptr, nullptr, n, w.partials, &w.st->counter, nullptr,
+        e = mgs_pass(o.dot_mode, w.q, nullptr, nullptr, nullptr, n, w.partials, &w.st->counter, nullptr,
                      &w.st->sumsq, nullptr, nullptr, s);
     if (e == cudaSuccess) {
         { ProfScope prof(PK_SMALL, s); gmres_init_kernel<<<1, 1, 0, s>>>(w.st, w.g, w.resid, k); }
         e = cudaGetLastError();
     }
     for (int j = 0; j < k && e == cudaSuccess; ++j) {
-        float *vj = w.V + size_t(j) * w.ldv;
-        // normalise v_j in place while building the projector's plane copies
-        e = launch_plane_copies(g, vj, &w.st->inv_norm, true, w.ob.Xc, w.ob.Yc, stop, s);
-        float *q = w.V + size_t(j + 1) * w.ldv;
+        // v_j = q / ||q|| stored in the basis while the projector's plane copies are built
+        e = launch_plane_copies(g, w.q, &w.st->inv_norm, w.vec(j), w.ob.Xc, w.ob.Yc, stop, s);
         if (e != cudaSuccess) break;
+        // q = B A v_j
         if (o.b_kind == CT_B_UN) {
             e = launch_joseph_A(g, w.ob.Xc, w.ob.Yc, w.ob.ypad, padded_layout(g), stop, s);
-            if (e == cudaSuccess) e = launch_voxel_B(g, w.ob.ypad, q, stop, s);
+            if (e == cudaSuccess) e = launch_voxel_B(g, w.ob.ypad, w.q, stop, s);
         } else {
             e = launch_joseph_A(g, w.ob.Xc, w.ob.Yc, w.ob.t, plain_layout(g), stop, s);
-            if (e == cudaSuccess) e = apply_B(g, o.b_kind, w.ob.t, nullptr, false, w.ob, q, stop, s, nullptr);
+            if (e == cudaSuccess) e = apply_B(g, o.b_kind, w.ob.t, nullptr, false, w.ob, w.q, stop, s, nullptr);
         }
-        if (e == cudaSuccess) e = arnoldi_orthogonalise(w, j, k, n, o, s);
+        if (e == cudaSuccess) e = arnoldi_orthogonalise(w, w.q, j, k, n, o, s);
     }
     if (e == cudaSuccess) {
         { ProfScope prof(PK_SMALL, s); backsolve_kernel<<<1, 1, 0, s>>>(w.R, w.g, w.y, w.st, k); }
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = combine(w.V, w.ldv, k, n, w.y, &w.st->iters, x, s);
+    if (e == cudaSuccess)
+        e = w.vbf16 ? combine_t(static_cast<const __nv_bfloat16 *>(w.V), w.ldv, k, n, w.y, &w.st->iters, x, s)
+                    : combine(static_cast<const float *>(w.V), w.ldv, k, n, w.y, &w.st->iters, x, s);
     if (e != cudaSuccess) {
         arena_close(ar);
         return cuda_error(e, "ct_bagmres_solve launch");
@@ -669,38 +779,158 @@ static ct_status abgmres(const ct_geom *geom, const float *b, int k, float *x, d
     if (rc != CT_OK) return rc;
     GmresWs w;
     carve_gmres(ar, g, k, true, o.b_kind, w);
+    float *Vf = static_cast<float *>(w.V);   // data-space basis, FP32
     const int *stop = &w.st->status;
     cudaError_t e = cudaMemsetAsync(w.st, 0, sizeof(SolverState), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.ob.ypad, 0, padded_sino_floats(g) * sizeof(float), s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(w.V, b, m * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Vf, b, m * sizeof(float), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess)
-        e = mgs_pass(o.dot_mode, w.V, nullptr, nullptr, nullptr, m, w.partials, &w.st->counter, nullptr,
+        e = mgs_pass(o.dot_mode, Vf, nullptr, nullptr, nullptr, m, w.partials, &w.st->counter, nullptr,
                      &w.st->sumsq, nullptr, nullptr, s);
     if (e == cudaSuccess) {
         { ProfScope prof(PK_SMALL, s); gmres_init_kernel<<<1, 1, 0, s>>>(w.st, w.g, w.resid, k); }
         e = cudaGetLastError();
     }
     for (int j = 0; j < k && e == cudaSuccess; ++j) {
-        float *vj = w.V + size_t(j) * w.ldv;
-        float *q = w.V + size_t(j + 1) * w.ldv;
+        float *vj = Vf + size_t(j) * w.ldv;
+        float *q = Vf + size_t(j + 1) * w.ldv;
         e = apply_B(g, o.b_kind, vj, &w.st->inv_norm, true, w.ob, w.tvol, stop, s, nullptr);
-        if (e == cudaSuccess) e = launch_plane_copies(g, w.tvol, nullptr, false, w.ob.Xc, w.ob.Yc, stop, s);
+        if (e == cudaSuccess) e = launch_plane_copies(g, w.tvol, nullptr, nullptr, w.ob.Xc, w.ob.Yc, stop, s);
         if (e == cudaSuccess) e = launch_joseph_A(g, w.ob.Xc, w.ob.Yc, q, plain_layout(g), stop, s);
-        if (e == cudaSuccess) e = arnoldi_orthogonalise(w, j, k, m, o, s);
+        if (e == cudaSuccess) e = arnoldi_orthogonalise(w, q, j, k, m, o, s);
     }
     if (e == cudaSuccess) {
         { ProfScope prof(PK_SMALL, s); backsolve_kernel<<<1, 1, 0, s>>>(w.R, w.g, w.y, w.st, k); }
         e = cudaGetLastError();
     }
     // u = V y (data space) into the last basis slot, then x = B u
-    float *u = w.V + size_t(k) * w.ldv;
-    if (e == cudaSuccess) e = combine(w.V, w.ldv, k, m, w.y, &w.st->iters, u, s);
+    float *u = Vf + size_t(k) * w.ldv;
+    if (e == cudaSuccess) e = combine(Vf, w.ldv, k, m, w.y, &w.st->iters, u, s);
     if (e == cudaSuccess) e = apply_B(g, o.b_kind, u, nullptr, false, w.ob, x, nullptr, s, nullptr);
     if (e != cudaSuccess) {
         arena_close(ar);
         return cuda_error(e, "ct_abgmres_solve launch");
     }
     rc = finish_solve(w.st, w.resid, k, resid_hist, iters_done, s, "ct_abgmres_solve");
+    arena_close(ar);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Gradient through a converged BA-GMRES solve.  x = (BA)^{-1} B b, so for a
+// scalar loss L(x) with gx = dL/dx:  dL/db = B^T (BA)^{-T} gx = B^T z with
+// (A^T B^T) z = gx.  z comes from GMRES on A^T B^T (image-space basis, built
+// afresh: the forward basis is not kept), each step applying B^T (voxel
+// splatting, then F^T for B_FBP) and A^T (ray scatter).
+// ---------------------------------------------------------------------------
+struct VjpWs {
+    GmresWs gm;
+    float *t = nullptr, *tf = nullptr;   // sinogram-space temporaries
+};
+
+static void carve_vjp(Arena &ar, const GeomDev &g, int k, int b_kind, VjpWs &w)
+{
+    const size_t n = size_t(g.nx) * g.ny * g.nz;
+    const size_t m = size_t(g.n_views) * g.nv * g.nu;
+    w.gm.ldv = round_ld(n);
+    w.gm.V = ar.take<float>(w.gm.ldv * size_t(k + 1));
+    w.t = ar.take<float>(m);
+    w.tf = b_kind == CT_B_FBP ? ar.take<float>(m) : nullptr;
+    const size_t ld = size_t(k) + 1;
+    w.gm.H = ar.take<double>(ld * k);
+    w.gm.H2 = ar.take<double>(ld);
+    w.gm.R = ar.take<double>(ld * k);
+    w.gm.cs = ar.take<double>(k);
+    w.gm.sn = ar.take<double>(k);
+    w.gm.g = ar.take<double>(ld);
+    w.gm.resid = ar.take<double>(ld);
+    w.gm.y = ar.take<double>(k);
+    w.gm.partials = ar.take<double>(partials_count());
+    w.gm.st = ar.take<SolverState>(1);
+}
+
+static size_t vjp_bytes(const GeomDev &g, int k, int b_kind)
+{
+    Arena ar;
+    ar.size = ~size_t(0) >> 1;
+    VjpWs w;
+    carve_vjp(ar, g, k, b_kind, w);
+    return ar.used;
+}
+
+__global__ void scale_vec_kernel(float *__restrict__ v, size_t len, const double *__restrict__ scale,
+                                 const int *__restrict__ stop)
+{
+    if (stop && *stop) return;
+    const float sc = float(*scale);
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < len; i += size_t(gridDim.x) * blockDim.x)
+        v[i] *= sc;
+}
+
+// out_sino = B^T vol (plain layout); b_kind B_UN or B_FBP
+static cudaError_t apply_Bt(const GeomDev &g, int b_kind, const float *vol, float *t, float *tf, float *out,
+                            const int *stop, cudaStream_t s)
+{
+    const size_t m = size_t(g.n_views) * g.nv * g.nu;
+    float *dst = b_kind == CT_B_FBP ? t : out;
+    cudaError_t e = cudaMemsetAsync(dst, 0, m * sizeof(float), s);
+    if (e == cudaSuccess) e = launch_voxel_Bt(g, vol, dst, stop, s);
+    if (e == cudaSuccess && b_kind == CT_B_FBP) e = launch_ramp(g, t, out, plain_layout(g), true, stop, s);
+    (void)tf;
+    return e;
+}
+
+static ct_status bagmres_vjp(const ct_geom *geom, const float *gx, int k, float *gb, double *resid_hist,
+                             const ct_solve_opts &o, int *iters_done, cudaStream_t s)
+{
+    if (o.b_kind == CT_B_AT)
+        return set_error(CT_EINVAL, "ct_bagmres_vjp: b_kind must be CT_B_UN or CT_B_FBP");
+    const GeomDev &g = geom->g;
+    const size_t n = geom->n;
+    Arena ar;
+    ct_status rc = open_ws(ar, vjp_bytes(g, k, o.b_kind), o, s);
+    if (rc != CT_OK) return rc;
+    VjpWs w;
+    carve_vjp(ar, g, k, o.b_kind, w);
+    GmresWs &gm = w.gm;
+    const int *stop = &gm.st->status;
+    const unsigned vb = red_blocks(n);
+    float *Vf = static_cast<float *>(gm.V);   // image-space basis, FP32
+    float *sino = o.b_kind == CT_B_FBP ? w.tf : w.t;   // B^T v lands here
+    cudaError_t e = cudaMemsetAsync(gm.st, 0, sizeof(SolverState), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Vf, gx, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = mgs_pass(o.dot_mode, Vf, nullptr, nullptr, nullptr, n, gm.partials, &gm.st->counter, nullptr,
+                     &gm.st->sumsq, nullptr, nullptr, s);
+    if (e == cudaSuccess) {
+        { ProfScope prof(PK_SMALL, s); gmres_init_kernel<<<1, 1, 0, s>>>(gm.st, gm.g, gm.resid, k); }
+        e = cudaGetLastError();
+    }
+    for (int j = 0; j < k && e == cudaSuccess; ++j) {
+        float *vj = Vf + size_t(j) * gm.ldv;
+        float *q = Vf + size_t(j + 1) * gm.ldv;
+        {
+            ProfScope prof(PK_CGLS_VEC, s);
+            scale_vec_kernel<<<vb, RED_BLOCK, 0, s>>>(vj, n, &gm.st->inv_norm, stop);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = apply_Bt(g, o.b_kind, vj, w.t, w.tf, sino, stop, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(q, 0, n * sizeof(float), s);
+        if (e == cudaSuccess) e = launch_joseph_At(g, sino, q, stop, s);
+        if (e == cudaSuccess) e = arnoldi_orthogonalise(gm, q, j, k, n, o, s);
+    }
+    if (e == cudaSuccess) {
+        { ProfScope prof(PK_SMALL, s); backsolve_kernel<<<1, 1, 0, s>>>(gm.R, gm.g, gm.y, gm.st, k); }
+        e = cudaGetLastError();
+    }
+    float *z = Vf + size_t(k) * gm.ldv;
+    if (e == cudaSuccess) e = combine(Vf, gm.ldv, k, n, gm.y, &gm.st->iters, z, s);
+    if (e == cudaSuccess) e = apply_Bt(g, o.b_kind, z, w.t, w.tf, gb, nullptr, s);
+    if (e != cudaSuccess) {
+        arena_close(ar);
+        return cuda_error(e, "ct_bagmres_vjp launch");
+    }
+    rc = finish_solve(gm.st, gm.resid, k, resid_hist, iters_done, s, "ct_bagmres_vjp");
     arena_close(ar);
     return rc;
 }
@@ -771,7 +1001,7 @@ static ct_status cgls(const ct_geom *geom, const float *b, int k, float *x, doub
     }
     for (int j = 1; j <= k && e == cudaSuccess; ++j) {
         // q = A p ; delta = ||q||^2
-        e = launch_plane_copies(g, w.p, nullptr, false, w.ob.Xc, w.ob.Yc, stop, s);
+        e = launch_plane_copies(g, w.p, nullptr, nullptr, w.ob.Xc, w.ob.Yc, stop, s);
         if (e == cudaSuccess) e = launch_joseph_A(g, w.ob.Xc, w.ob.Yc, w.q, plain_layout(g), stop, s);
         if (e == cudaSuccess)
             e = mgs_pass(1, w.q, nullptr, nullptr, nullptr, m, w.partials, ctr, nullptr, &st->delta, stop, nullptr, s);
@@ -789,7 +1019,7 @@ static ct_status cgls(const ct_geom *geom, const float *b, int k, float *x, doub
             e = cudaGetLastError();
         }
         if (e == cudaSuccess && data) {
-            e = launch_plane_copies(g, x, nullptr, false, w.ob.Xc, w.ob.Yc, stop, s);
+            e = launch_plane_copies(g, x, nullptr, nullptr, w.ob.Xc, w.ob.Yc, stop, s);
             if (e == cudaSuccess) e = launch_joseph_A(g, w.ob.Xc, w.ob.Yc, w.ax, plain_layout(g), stop, s);
             if (e == cudaSuccess) {
                 { ProfScope prof(PK_CGLS_VEC, s); diff_sumsq_kernel<<<vb, RED_BLOCK, 0, s>>>(b, w.ax, m, w.partials, ctr, &st->data_rr, stop); }
@@ -839,6 +1069,7 @@ size_t ct_workspace_bytes(const ct_geom *geom, int k, int solver, const ct_solve
     case CT_SOLVER_BA: return gmres_bytes(geom->g, k, false, o.b_kind);
     case CT_SOLVER_AB: return gmres_bytes(geom->g, k, true, o.b_kind);
     case CT_SOLVER_CGLS: return cgls_ws_bytes(geom->g, k, o.record_data_resid != 0);
+    case CT_SOLVER_BA_VJP: return vjp_bytes(geom->g, k, o.b_kind);
     default: return 0;
     }
 }
@@ -868,6 +1099,17 @@ ct_status ct_cgls_solve(const ct_geom *geom, const float *b_dev, int k, float *x
     ct_status rc = check_common(geom, b_dev, k, x_out_dev, &o);
     if (rc != CT_OK) return rc;
     return cgls(geom, b_dev, k, x_out_dev, resid_hist, o, iters_done, static_cast<cudaStream_t>(stream));
+}
+
+ct_status ct_bagmres_vjp(const ct_geom *geom, const float *gx_dev, int k, float *gb_dev, double *resid_hist,
+                         const ct_solve_opts *opts, int *iters_done, void *stream)
+{
+    ct_solve_opts o = resolve_opts(opts);
+    if (!geom || !gx_dev || !gb_dev) return set_error(CT_EINVAL, "ct_bagmres_vjp: NULL argument");
+    if (k < 1 || k > 4096) return set_error(CT_EINVAL, "ct_bagmres_vjp: k must be in [1, 4096] (got %d)", k);
+    if (o.dot_mode != 0 && o.dot_mode != 1) return set_error(CT_EINVAL, "ct_bagmres_vjp: dot_mode must be 0 or 1");
+    if (!(o.tol >= 0.0)) return set_error(CT_EINVAL, "ct_bagmres_vjp: tol must be >= 0");
+    return bagmres_vjp(geom, gx_dev, k, gb_dev, resid_hist, o, iters_done, static_cast<cudaStream_t>(stream));
 }
 
 ct_status ct_mgs_sweep(const float *V_dev, size_t ldv, int j, size_t len, float *q_dev, double *h_dev,

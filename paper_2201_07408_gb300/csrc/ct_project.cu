@@ -92,58 +92,78 @@ __device__ __forceinline__ RaySetup ray_setup(const GeomDev &g, int s, int iv, i
 
 // ---------------------------------------------------------------------------
 // Plane-major zero-bordered copies.  One block handles a 32x32 (x, y) tile
-// of one padded z slice; Yc rows are written straight from the tile, Xc rows
-// from its transpose in shared memory.
+// of one padded z slice, read with a one-voxel halo so that bf16 pairs
+// (b, b+1) can be formed; Yc rows are written straight from the tile, Xc
+// rows from its transpose in shared memory.  When a basis slot is given the
+// scaled volume is stored there too (each voxel by the tile that owns it).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) plane_copies_kernel(GeomDev g, float *__restrict__ vol,
+template <bool BF>
+__global__ void __launch_bounds__(256) plane_copies_kernel(GeomDev g, const float *__restrict__ vol,
                                                            const double *__restrict__ scale,
-                                                           int normalize_inplace,
-                                                           float *__restrict__ Xc,
-                                                           float *__restrict__ Yc,
+                                                           void *__restrict__ basis_out,
+                                                           float *__restrict__ Xc, float *__restrict__ Yc,
                                                            const int *__restrict__ stop)
 {
     if (stop && *stop) return;
-    __shared__ float tile[32][33];
+    __shared__ float tile[33][33];
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    const int tid = ty * 32 + tx;
     const int xp0 = blockIdx.x * 32, yp0 = blockIdx.y * 32;  // padded tile origin
     const int zp = blockIdx.z;
     const int z = zp - PAD_A;
     const float sc = scale ? float(*scale) : 1.0f;
     const bool zin = z >= 0 && z < g.nz;
-    for (int r = ty; r < 32; r += 8) {
-        const int x = xp0 + tx - PAD_A, y = yp0 + r - PAD_A;
+    for (int i = tid; i < 33 * 33; i += 256) {
+        const int r = i / 33, c = i - r * 33;
+        const int x = xp0 + c - PAD_A, y = yp0 + r - PAD_A;
         float val = 0.0f;
         if (zin && x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
             const size_t idx = (size_t(z) * g.ny + y) * g.nx + x;
             val = vol[idx] * sc;
-            if (normalize_inplace) vol[idx] = val;
+            if (basis_out && r < 32 && c < 32) {
+                if (BF)
+                    static_cast<__nv_bfloat16 *>(basis_out)[idx] = __float2bfloat16_rn(val);
+                else
+                    static_cast<float *>(basis_out)[idx] = val;
+            }
         }
-        tile[r][tx] = val;
+        tile[r][c] = val;
     }
     __syncthreads();
     // Yc[zp][y][xp] for y in the grid, xp over the padded row
     for (int r = ty; r < 32; r += 8) {
         const int y = yp0 + r - PAD_A, xp = xp0 + tx;
-        if (y >= 0 && y < g.ny && xp < g.pitchY)
-            Yc[(size_t(zp) * g.ny + y) * g.pitchY + xp] = tile[r][tx];
+        if (y >= 0 && y < g.ny && xp < g.pitchY) {
+            const size_t o = (size_t(zp) * g.ny + y) * g.pitchY + xp;
+            if (BF)
+                reinterpret_cast<uint32_t *>(Yc)[o] = pack_bf16x2(tile[r][tx], tile[r][tx + 1]);
+            else
+                Yc[o] = tile[r][tx];
+        }
     }
     // Xc[zp][x][yp] for x in the grid, yp over the padded row
     for (int r = ty; r < 32; r += 8) {
         const int x = xp0 + r - PAD_A, yp = yp0 + tx;
-        if (x >= 0 && x < g.nx && yp < g.pitchX)
-            Xc[(size_t(zp) * g.nx + x) * g.pitchX + yp] = tile[tx][r];
+        if (x >= 0 && x < g.nx && yp < g.pitchX) {
+            const size_t o = (size_t(zp) * g.nx + x) * g.pitchX + yp;
+            if (BF)
+                reinterpret_cast<uint32_t *>(Xc)[o] = pack_bf16x2(tile[tx][r], tile[tx + 1][r]);
+            else
+                Xc[o] = tile[tx][r];
+        }
     }
 }
 
-cudaError_t launch_plane_copies(const GeomDev &g, float *vol, const double *scale,
-                                bool normalize_inplace, float *Xc, float *Yc, const int *stop,
-                                cudaStream_t st)
+cudaError_t launch_plane_copies(const GeomDev &g, const float *vol, const double *scale, void *basis_out,
+                                float *Xc, float *Yc, const int *stop, cudaStream_t st)
 {
     ProfScope prof(PK_PLANE_COPIES, st);
     dim3 block(32, 8);
     dim3 grid((g.nx + 2 * PAD_A + 31) / 32, (g.ny + 2 * PAD_A + 31) / 32, g.nzp);
-    plane_copies_kernel<<<grid, block, 0, st>>>(g, vol, scale, normalize_inplace ? 1 : 0, Xc, Yc,
-                                                stop);
+    if (g.vol_bf16)
+        plane_copies_kernel<true><<<grid, block, 0, st>>>(g, vol, scale, basis_out, Xc, Yc, stop);
+    else
+        plane_copies_kernel<false><<<grid, block, 0, st>>>(g, vol, scale, basis_out, Xc, Yc, stop);
     return cudaGetLastError();
 }
 
@@ -164,7 +184,30 @@ cudaError_t launch_plane_copies(const GeomDev &g, float *vol, const double *scal
 // ---------------------------------------------------------------------------
 constexpr int A_BLOCK = 128;
 
-template <int VR, bool WINDOW, bool ZCLAMP>
+// b-interpolated value of one plane row: (1 - wb) V[b0] + wb V[b0+1], read as
+// two floats or as one packed bf16 pair
+template <bool BF>
+__device__ __forceinline__ float row_lerp(const float *p, float wb)
+{
+    if (BF) {
+        const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(p));
+        const float v0 = bf16_lo(w), v1 = bf16_hi(w);
+        return fmaf(wb, v1 - v0, v0);
+    }
+    const float v0 = __ldg(p), v1 = __ldg(p + 1);
+    return fmaf(wb, v1 - v0, v0);
+}
+
+// rays per thread along a detector column, and plane-loop unroll (tuning)
+#ifndef CT_A_VR
+#define CT_A_VR 8
+#endif
+#ifndef CT_A_PUNROLL
+#define CT_A_PUNROLL 2
+#endif
+constexpr int kAPlaneUnroll = CT_A_PUNROLL;
+
+template <int VR, bool WINDOW, bool ZCLAMP, bool BF>
 __global__ void __launch_bounds__(A_BLOCK) joseph_A_kernel(GeomDev g, const float *__restrict__ Xc,
                                                            const float *__restrict__ Yc,
                                                            float *__restrict__ y, SinoLayout lay,
@@ -230,6 +273,7 @@ __global__ void __launch_bounds__(A_BLOCK) joseph_A_kernel(GeomDev g, const floa
 #pragma unroll
     for (int i = 0; i < VR; ++i) acc[i] = 0.0f;
 
+#pragma unroll kAPlaneUnroll
     for (int p = p0; p <= p1; ++p) {
         const float pm = float(p) - ca;
         const float fb = fmaf(pm, gb, fbc);
@@ -250,13 +294,10 @@ __global__ void __launch_bounds__(A_BLOCK) joseph_A_kernel(GeomDev g, const floa
             const float wz = fz - z0f;
             const int z0 = ZCLAMP ? min(max(int(z0f), -PAD_A), zmax) : int(z0f);
             const float *r = rowp + (z0 + 1) * zstride;
-            const float h0 = __ldg(r), h1 = __ldg(r + 1);
-            const float hi = fmaf(wb, h1 - h0, h0);
+            const float hi = row_lerp<BF>(r, wb);
             float lo;
             if (!WINDOW || i == 0) {
-                const float *rl = r - zstride;
-                const float l0 = __ldg(rl), l1 = __ldg(rl + 1);
-                lo = fmaf(wb, l1 - l0, l0);
+                lo = row_lerp<BF>(r - zstride, wb);
             } else {
                 // z0 is z_prev or z_prev + 1: the low row is one of the previous rows
                 lo = z0 == z_prev ? lo_prev : hi_prev;
@@ -281,24 +322,37 @@ __global__ void __launch_bounds__(A_BLOCK) joseph_A_kernel(GeomDev g, const floa
     }
 }
 
+template <bool BF>
+static void launch_joseph_A_t(const GeomDev &g, const float *Xc, const float *Yc, float *y, SinoLayout lay,
+                              const int *stop, cudaStream_t st)
+{
+    constexpr int WPB = A_BLOCK / 32;
+    if (g.nv == 1) {
+        dim3 grid((g.nu + 31) / 32, (g.nv + WPB - 1) / WPB, g.n_views);
+        joseph_A_kernel<1, false, true, BF><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
+        return;
+    }
+    constexpr int VR = CT_A_VR;
+    dim3 grid((g.nu + 31) / 32, (g.nv + WPB * VR - 1) / (WPB * VR), g.n_views);
+#ifndef CT_A_FORCE_ZCLAMP
+#define CT_A_FORCE_ZCLAMP 0
+#endif
+    if (g.a_window && g.a_zsafe && !CT_A_FORCE_ZCLAMP)
+        joseph_A_kernel<VR, true, false, BF><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
+    else if (g.a_window)
+        joseph_A_kernel<VR, true, true, BF><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
+    else
+        joseph_A_kernel<VR, false, true, BF><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
+}
+
 cudaError_t launch_joseph_A(const GeomDev &g, const float *Xc, const float *Yc, float *y,
                             SinoLayout lay, const int *stop, cudaStream_t st)
 {
     ProfScope prof(PK_JOSEPH_A, st);
-    constexpr int WPB = A_BLOCK / 32;
-    if (g.nv == 1) {
-        dim3 grid((g.nu + 31) / 32, (g.nv + WPB - 1) / WPB, g.n_views);
-        joseph_A_kernel<1, false, true><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
-    } else {
-        constexpr int VR = 8;
-        dim3 grid((g.nu + 31) / 32, (g.nv + WPB * VR - 1) / (WPB * VR), g.n_views);
-        if (g.a_window && g.a_zsafe)
-            joseph_A_kernel<VR, true, false><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
-        else if (g.a_window)
-            joseph_A_kernel<VR, true, true><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
-        else
-            joseph_A_kernel<VR, false, true><<<grid, A_BLOCK, 0, st>>>(g, Xc, Yc, y, lay, stop);
-    }
+    if (g.vol_bf16)
+        launch_joseph_A_t<true>(g, Xc, Yc, y, lay, stop, st);
+    else
+        launch_joseph_A_t<false>(g, Xc, Yc, y, lay, stop, st);
     return cudaGetLastError();
 }
 
@@ -370,8 +424,7 @@ extern "C" ct_status ct_project_A(const ct_geom *geom, const float *x_dev, float
     if (rc != CT_OK) return rc;
     float *Xc = ar.take<float>(size_t(g.nzp) * g.nx * g.pitchX);
     float *Yc = ar.take<float>(size_t(g.nzp) * g.ny * g.pitchY);
-    cudaError_t e = launch_plane_copies(g, const_cast<float *>(x_dev), nullptr, false, Xc, Yc,
-                                        nullptr, st);
+    cudaError_t e = launch_plane_copies(g, x_dev, nullptr, nullptr, Xc, Yc, nullptr, st);
     if (e == cudaSuccess) e = launch_joseph_A(g, Xc, Yc, y_dev, plain_layout(g), nullptr, st);
     arena_close(ar);
     if (e != cudaSuccess) return cuda_error(e, "ct_project_A launch");
@@ -434,7 +487,7 @@ extern "C" ct_status ct_project_A_noalloc(const ct_geom *geom, const float *x_de
     float *Xc = base;
     float *Yc = base + xc_bytes / sizeof(float);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_plane_copies(g, const_cast<float *>(x_dev), nullptr, false, Xc, Yc, nullptr, st);
+    cudaError_t e = launch_plane_copies(g, x_dev, nullptr, nullptr, Xc, Yc, nullptr, st);
     if (e == cudaSuccess) e = launch_joseph_A(g, Xc, Yc, y_dev, plain_layout(g), nullptr, st);
     if (e != cudaSuccess) return cuda_error(e, "ct_project_A_noalloc launch");
     return CT_OK;

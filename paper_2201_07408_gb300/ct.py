@@ -23,7 +23,7 @@ CT_OK, CT_EINVAL, CT_ENOMEM, CT_ECUDA, CT_ENONFINITE, CT_ETIMEOUT, CT_BREAKDOWN_
 CT_PARALLEL_2D, CT_CONE_3D = 0, 1
 CT_F32, CT_BF16 = 0, 1
 CT_B_UN, CT_B_FBP, CT_B_AT = 0, 1, 2
-CT_SOLVER_BA, CT_SOLVER_AB, CT_SOLVER_CGLS = 0, 1, 2
+CT_SOLVER_BA, CT_SOLVER_AB, CT_SOLVER_CGLS, CT_SOLVER_BA_VJP = 0, 1, 2, 3
 
 B_KINDS = {"un": CT_B_UN, "fbp": CT_B_FBP, "at": CT_B_AT, "At": CT_B_AT}
 
@@ -63,6 +63,7 @@ SIGNATURES = {
     "ct_bagmres_solve": (_i, [_vp, _vp, _i, _vp, _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
     "ct_abgmres_solve": (_i, [_vp, _vp, _i, _vp, _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
     "ct_cgls_solve": (_i, [_vp, _vp, _i, _vp, _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
+    "ct_bagmres_vjp": (_i, [_vp, _vp, _i, _vp, _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
     "ct_workspace_bytes": (_sz, [_vp, _i, _i, _P(ct_solve_opts)]),
     "ct_mgs_sweep": (_i, [_vp, _sz, _i, _sz, _vp, _vp, _i, _vp]),
     "ct_basis_combine": (_i, [_vp, _sz, _i, _sz, _vp, _vp, _vp]),
@@ -136,12 +137,12 @@ class Geometry:
     sod, sdd."""
 
     def __init__(self, kind, nx, ny, nz, vox, n_views, ang0, span, nu, nv, du, dv, sod=0.0, sdd=0.0,
-                 device=None):
+                 device=None, vol_dtype=CT_F32, sino_dtype=CT_F32):
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
                                    else torch.device(device).index or 0)
         self.desc = ct_geom_desc(int(kind), int(nx), int(ny), int(nz), float(vox), int(n_views), float(ang0),
                                  float(span), int(nu), int(nv), float(du), float(dv), float(sod), float(sdd),
-                                 CT_F32, CT_F32)
+                                 _dtype(vol_dtype), _dtype(sino_dtype))
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check("ct_geom_create", lib().ct_geom_create(ctypes.byref(self.desc), ctypes.byref(self._h)))
@@ -151,9 +152,10 @@ class Geometry:
         self.sino_shape = (int(n_views), int(nv), int(nu))
 
     @classmethod
-    def from_spec(cls, spec, device=None):
+    def from_spec(cls, spec, device=None, vol_dtype=CT_F32, sino_dtype=CT_F32):
         return cls(spec.kind, spec.nx, spec.ny, spec.nz, spec.vox, spec.n_views, spec.ang0, spec.span,
-                   spec.nu, spec.nv, spec.du, spec.dv, spec.sod, spec.sdd, device=device)
+                   spec.nu, spec.nv, spec.du, spec.dv, spec.sod, spec.sdd, device=device,
+                   vol_dtype=vol_dtype, sino_dtype=sino_dtype)
 
     @property
     def handle(self):
@@ -169,6 +171,16 @@ class Geometry:
             self.close()
         except Exception:
             pass
+
+
+def _dtype(d) -> int:
+    if isinstance(d, str):
+        return {"f32": CT_F32, "fp32": CT_F32, "bf16": CT_BF16}[d]
+    if d is torch.bfloat16:
+        return CT_BF16
+    if d is torch.float32:
+        return CT_F32
+    return int(d)
 
 
 def _bkind(b_kind) -> int:
@@ -276,6 +288,26 @@ def ct_cgls_solve(geom, b, k, x_out, opts=None, stream=None, workspace="torch") 
     """CGLS with back-projector opts.b_kind in place of A^T (Eqs. 2-3)."""
     return _solve("ct_cgls_solve", lib().ct_cgls_solve, CT_SOLVER_CGLS, geom, b, k, x_out, opts, stream,
                   workspace)
+
+
+def ct_bagmres_vjp(geom, gx, k, gb_out, opts=None, stream=None, workspace="torch") -> SolveResult:
+    """dL/db = B^T (A^T B^T)^{-1} gx through a converged BA-GMRES solve
+    (k GMRES iterations on A^T B^T); gb_out (m floats) receives it."""
+    d = geom.device
+    if opts is None:
+        opts = make_opts()
+    if workspace == "torch":
+        nbytes = ct_workspace_bytes(geom, k, CT_SOLVER_BA_VJP, opts)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=d)
+        opts.workspace = ctypes.c_void_p(ws.data_ptr())
+        opts.workspace_bytes = nbytes
+    resid = np.zeros(int(k) + 1, dtype=np.float64)
+    iters = ctypes.c_int(0)
+    st = lib().ct_bagmres_vjp(geom.handle, _ptr(gx, geom.n, "gx", d), int(k), _ptr(gb_out, geom.m, "gb", d),
+                              resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opts),
+                              ctypes.byref(iters), _stream(stream, d))
+    _check("ct_bagmres_vjp", st, allow=(CT_OK, CT_BREAKDOWN_LUCKY))
+    return SolveResult(status=st, iters=iters.value, resid=resid)
 
 
 def ct_mgs_sweep(V, ldv, j, length, q, h, dot_mode=0, stream=None):

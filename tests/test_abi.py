@@ -62,7 +62,7 @@ def _desc(libct, **kw):
 
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(n_views=-1), dict(voxel_mm=0.0), dict(kind=7),
                                  dict(kind=0, nz=4), dict(kind=0, nz=1, nv=3), dict(sdd_mm=400.0),
-                                 dict(nx=2000, ny=2000, voxel_mm=1.0), dict(vol_dtype=5),
+                                 dict(nx=2000, ny=2000, voxel_mm=1.0), dict(vol_dtype=5), dict(sino_dtype=7),
                                  dict(du_mm=-1.0), dict(angle_span_rad=float("nan"))])
 def test_geometry_validation_rejects_bad_descriptions(libct, bad):
     h = ctypes.c_void_p()
