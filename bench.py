@@ -50,8 +50,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"],
                     help="storage of the working copies and the Krylov basis (arithmetic stays FP32)")
-    ap.add_argument("--op", default=None, choices=["A", "B", "Bfbp", "F", "At", "Bt", "mgs"],
-                    help="time one operator of the workload instead of the solve (profiling aid)")
+    ap.add_argument("--op", default=None,
+                    choices=["A", "B", "Bfbp", "F", "At", "Bt", "mgs", "ba", "ab", "cgls", "vjp"],
+                    help="time one operator, or one whole solve (ba, ab, cgls: --iters iterations with "
+                         "B_FBP; vjp: the adjoint GMRES of the gradient), instead of the headline step")
     return ap.parse_args()
 
 
@@ -66,6 +68,24 @@ def dist_env():
 # CPU baseline: the FP64 oracle as it stands, on a bounded sample of one
 # BA-GMRES iteration of the same workload, extrapolated per iteration.
 # ---------------------------------------------------------------------------
+def host_info():
+    """Architecture, core count, OpenMP setting and CPU model of the host."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    return {"arch": platform.machine(), "nproc": os.cpu_count(),
+            "omp_num_threads": os.environ.get("OMP_NUM_THREADS"), "cpu_model": model}
+
+
 def oracle_iteration_sample(spec, x_true, b, k, frac=1.0 / 48, seed=5):
     import oracle
     threads = oracle.num_threads()
@@ -178,6 +198,36 @@ def aggregate_over_ranks(elapsed_s, iters, world, device=None):
     return elapsed_max, float(n.item()), float(n.item()) / elapsed_max
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture of the kernel on the workload, with the SHA-256 of the
+# kernel's source file at capture time: a changed source gives null (the
+# counters no longer describe the kernel).  The captures are summarised in
+# profiles/.
+NCU_TRAFFIC = {
+    # (kernel, storage, workload): (bytes per launch, source file, sha256)
+    ("voxel_B", "f32", "cone_256"): (1416911000 + 68460800, "ct_backproject.cu",
+                                     "7b9ee25c3dcf6eacb3dd60ffb78a49a48378d98654ea43a5d68915322ae668b0"),
+    ("joseph_A", "f32", "cone_256"): (393732352 + 132797696, "ct_project.cu",
+                                      "a7e46fb88ec1cdb0f29666cfb41c9894698e099b53ed0a9defb18fb89d061c23"),
+}
+
+
+def ncu_traffic(kernel, storage, workload):
+    import hashlib
+    ent = NCU_TRAFFIC.get((kernel, storage, workload))
+    if not ent:
+        return None
+    nbytes, src, sha = ent
+    path = os.path.join(ROOT, "paper_2201_07408_gb300", "csrc", src)
+    try:
+        with open(path, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != sha:
+                return None
+    except OSError:
+        return None
+    return nbytes
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -222,13 +272,13 @@ def run_reference(args, world, rank):
             times.append(last["sec_per_iter"])
     sec = statistics.median(times)
     value = 1.0 / sec
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * args.iters * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": spec.name, "iters_per_step": args.iters,
                                             "b_kind": B_KIND},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
-                             "sample": last["sample"]},
+                             "sample": last["sample"], "host": host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -305,19 +355,16 @@ def run_ours(args, world, rank, local):
     launches = sum(c for _, c in prof.values())
     kernel_ms = {kk: round(v[0] / max(args.steps, 1), 3) for kk, v in prof.items() if v[1]}
 
-    # e2e: host data in, image out, every step
+    # e2e: the C-ABI call with host buffers (pinned), copies inside the call
     b_pin = torch.from_numpy(b_host).pin_memory()
     x_pin = torch.empty(spec.vol_shape, dtype=torch.float32).pin_memory()
-    b_e2e = torch.empty_like(b)
     steps_e2e = max(1, min(args.steps, 3))
+    ct.ct_bagmres_solve_host(g, b_pin, k, x_pin, opts, workspace=None)   # allocator pool warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     it_e2e = 0
     for _ in range(steps_e2e):
-        b_e2e.copy_(b_pin, non_blocking=True)
-        r = ct.ct_bagmres_solve(g, b_e2e, k, x, opts, workspace=None)
-        x_pin.copy_(x, non_blocking=True)
-        torch.cuda.synchronize()
+        r = ct.ct_bagmres_solve_host(g, b_pin, k, x_pin, opts, workspace=None)
         it_e2e += r.iters
     e2e_sec = time.perf_counter() - t0
     e2e_value = it_e2e / e2e_sec * world
@@ -334,17 +381,31 @@ def run_ours(args, world, rank, local):
         alg_bytes = 4.0 * (spec.n + spec.m)
         dom_ms = b_ms
     achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
-    # FP32 issue-rate roofline of the same kernel: ~12 flops per sample
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    # FP32 roofline of the same kernel: 12 flops per A sample, 14 per B sample
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = sms * 128 * 2 * 2070e6 / 1e12
-    flops = 12.0 * (a_samples if dom[0] == "joseph_A" else b_samples)
+    samples = a_samples if dom[0] == "joseph_A" else b_samples
+    flops = (12.0 if dom[0] == "joseph_A" else 14.0) * samples
     alu_achieved = flops / (dom_ms * 1e-3) / 1e12
+    # gather rate: 16 bytes (the four neighbours) per sample, against the SM
+    # load data path (128 bytes per SM per clock)
+    l1_peak = sms * 128 * 2070e6 / 1e9
+    gather = samples * 16.0 / (dom_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(dom[0], args.storage, spec.name)
     roofline = {"kernel": dom[0], "bound": "alu", "achieved": round(alu_achieved, 3),
                 "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(alu_achieved / fp32_peak, 4),
-                "traffic": None, "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x 2070 MHz" % sms,
+                "traffic": traffic, "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x 2070 MHz" % sms,
                 "hbm": {"achieved_gbs": round(achieved, 1), "peak_gbs": hbm_peak, "peak_source": peak_src,
-                        "frac": round(achieved / hbm_peak, 4), "alg_bytes": alg_bytes}}
+                        "frac": round(achieved / hbm_peak, 4), "alg_bytes": alg_bytes},
+                "gather": {"achieved_gbs": round(gather, 1), "peak_gbs": round(l1_peak, 1),
+                           "frac": round(gather / l1_peak, 4),
+                           "peak_source": "derived: %d SMs x 128 B/clk x 2070 MHz" % sms}}
+    # time to a relative residual of 1e-2 (iterations from the last solve's history)
+    hist = res.resid[:res.iters + 1] / res.resid[0]
+    hit = np.nonzero(hist <= 1e-2)[0]
+    ms_per_iter = elapsed_max / max(iters_done, 1) * 1e3
+    ttr = {"iters": int(hit[0]) if hit.size else None,
+           "ms": round(float(hit[0]) * ms_per_iter, 3) if hit.size else None}
 
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(elapsed_max / args.steps * 1e3, 3),
@@ -358,9 +419,11 @@ def run_ours(args, world, rank, local):
                              % ((k + 1) * spec.n * 4 / 1e9)},
             "A_gsamples_per_s": round(a_gs, 3), "B_gsamples_per_s": round(b_gs, 3),
             "kernel_ms_per_step": kernel_ms, "resid_final_rel": float(res.resid[res.iters] / res.resid[0]),
+            "time_to_resid_1e-2": ttr,
             "clocks": clocks, "gpu_launches": int(launches), "roofline": roofline,
             "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": int(spec.m * 4),
-                    "d2h_bytes_per_step": int(spec.n * 4 + (k + 1) * 8)}}
+                    "d2h_bytes_per_step": int(spec.n * 4 + (k + 1) * 8),
+                    "call": "ct_bagmres_solve_host (pinned host b and x)"}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_iteration_sample(spec, x_true, b_host, k, frac=0.5)
         # relative error of the GPU operators on the oracle's samples
@@ -372,7 +435,7 @@ def run_ours(args, world, rank, local):
                                      "F": rel_err(fr.double().cpu().numpy(), cb["f_rows"])}
         line["cpu_baseline"] = {"value": round(1.0 / cb["sec_per_iter"], 6), "unit": UNIT, "cores": cb["cores"],
                                 "kind": "oracle", "sample": cb["sample"],
-                                "cpu_seconds": round(cb["cpu_seconds"], 2)}
+                                "cpu_seconds": round(cb["cpu_seconds"], 2), "host": host_info()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -396,6 +459,14 @@ def run_op(args):
     out_s = torch.empty(spec.sino_shape, device=dev)
     j = 20
     V = q = h = None
+    solver_opts = ct.make_opts(b_kind="un" if args.op == "cgls" else "fbp")
+    if args.op in ("ba", "ab", "cgls", "vjp"):
+        kind = {"ba": ct.CT_SOLVER_BA, "ab": ct.CT_SOLVER_AB, "cgls": ct.CT_SOLVER_CGLS,
+                "vjp": ct.CT_SOLVER_BA_VJP}[args.op]
+        nbytes = ct.ct_workspace_bytes(g, args.iters, kind, solver_opts)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        solver_opts.workspace = ws.data_ptr()
+        solver_opts.workspace_bytes = nbytes
     if args.op == "mgs":
         ldv = (spec.n + 63) // 64 * 64
         V = torch.randn(j * ldv, device=dev) / math.sqrt(spec.n)
@@ -407,7 +478,11 @@ def run_op(args):
           "F": lambda: ct.ct_ramp_F(g, y, out_s),
           "At": lambda: ct.ct_adjoint_At(g, y, out_v),
           "Bt": lambda: ct.ct_adjoint_Bt(g, x, out_s, "un"),
-          "mgs": lambda: ct.ct_mgs_sweep(V, (spec.n + 63) // 64 * 64, j, spec.n, q, h)}[args.op]
+          "mgs": lambda: ct.ct_mgs_sweep(V, (spec.n + 63) // 64 * 64, j, spec.n, q, h),
+          "ba": lambda: ct.ct_bagmres_solve(g, y, args.iters, out_v, solver_opts, workspace=None),
+          "ab": lambda: ct.ct_abgmres_solve(g, y, args.iters, out_v, solver_opts, workspace=None),
+          "cgls": lambda: ct.ct_cgls_solve(g, y, args.iters, out_v, solver_opts, workspace=None),
+          "vjp": lambda: ct.ct_bagmres_vjp(g, x, args.iters, out_s, solver_opts, workspace=None)}[args.op]
     for _ in range(args.warmup):
         fn()
     torch.cuda.synchronize()
@@ -423,7 +498,12 @@ def run_op(args):
     ct.profile_enable(False)
     prof = {k: v for k, v in ct.profile_read().items() if v[1]}
     ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"op": args.op, "workload": spec.name, "storage": args.storage, "ms_per_call": round(ms, 4),
+    extra = {}
+    if args.op in ("ba", "ab", "cgls", "vjp"):
+        extra = {"iters": args.iters, "ms_per_iter": round(ms / args.iters, 4),
+                 "b_kind": "un" if args.op == "cgls" else "fbp"}
+    print(json.dumps({"op": args.op, **extra, "workload": spec.name, "storage": args.storage,
+                      "ms_per_call": round(ms, 4),
                       "kernels": {k: {"ms_per_launch": round(v[0] / v[1], 4), "launches": v[1]}
                                   for k, v in prof.items()},
                       "joseph_samples": spec.joseph_samples(), "voxel_view_samples": spec.voxel_view_samples()}),

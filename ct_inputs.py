@@ -112,12 +112,15 @@ CONE_GRAD32 = _cone("cone_grad32", 32, 4.0, 128, 48, 32, 6.0)
 CONE_SMALL = _cone("cone_small", 44, 128.0 / 44, 60, 66, 44, 288.0 / 66)
 CONE_ANISO = _cone("cone_aniso", 0, 3.0, 45, 70, 30, 4.0, nxyz=(40, 36, 28),
                    ang0=0.3, dv=4.5)
+# a slab thinner than the back-projector's z run (5 slices) on a detector
+# whose row count (7) is not a multiple of the projector's rays per thread
+CONE_THIN = _cone("cone_thin", 0, 2.5, 36, 50, 7, 3.5, nxyz=(30, 26, 5), ang0=0.2)
 PAR2D_ANISO = Geometry(name="par2d_aniso", kind=PARALLEL_2D, nx=37, ny=29, nz=1,
                        vox=1.3, n_views=41, ang0=0.1, span=math.pi, nu=53, nv=1,
                        du=1.1, dv=1.0)
 
 WORKLOADS = {g.name: g for g in (PAR2D_64, CONE_128, CONE_256, CONE_512, CONE_512_CUT64,
-                                 CONE_GRAD32, CONE_SMALL, CONE_ANISO, PAR2D_ANISO)}
+                                 CONE_GRAD32, CONE_SMALL, CONE_ANISO, CONE_THIN, PAR2D_ANISO)}
 
 
 def scaled(g: Geometry, **kw) -> Geometry:
@@ -237,8 +240,10 @@ def phantom(g: Geometry, seed=0, dtype=np.float32):
         ells = random_ellipses_2d(10, seed=seed, radius=0.5 * min(g.nx, g.ny) * g.vox)
     else:
         fov = min(g.nx, g.ny) * g.vox
-        ells = random_ellipsoids(12, seed=seed, scale=fov / 128.0,
-                                 z_half=min(40.0, 0.45 * g.nz * g.vox * 128.0 / fov))
+        z_half = min(40.0, 0.45 * g.nz * g.vox * 128.0 / fov)
+        # slabs thinner than the largest ellipsoid get proportionally smaller ones
+        semi = (5.0, 30.0) if z_half > 34.0 else (0.15 * z_half, 0.85 * z_half)
+        ells = random_ellipsoids(12, seed=seed, scale=fov / 128.0, z_half=z_half, semi_range=semi)
     return voxelize(g, ells, dtype=dtype), ells
 
 

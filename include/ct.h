@@ -172,6 +172,19 @@ CT_API ct_status ct_bagmres_solve(const ct_geom *geom, const float *b_dev, int k
                            double *resid_hist, const ct_solve_opts *opts, int *iters_done,
                            void *stream);
 
+/* ct_bagmres_solve with the data and the image in HOST memory: b_host (m
+ * floats) is copied to the device, the solve runs as ct_bagmres_solve, and
+ * x_k is copied back into x_out_host (n floats) before the call returns.
+ * The two device vectors are taken from the stream-ordered allocator
+ * (cudaMallocAsync) on `stream` and freed before return; the workspace is
+ * as for ct_bagmres_solve.  Page-locked host buffers give asynchronous
+ * copies; pageable ones work too.  Synchronous: on return x_out_host and
+ * resid_hist hold the result.  Returns CT_ENOMEM when the device vectors
+ * cannot be allocated; other codes as ct_bagmres_solve. */
+CT_API ct_status ct_bagmres_solve_host(const ct_geom *geom, const float *b_host, int k, float *x_out_host,
+                                       double *resid_hist, const ct_solve_opts *opts, int *iters_done,
+                                       void *stream);
+
 /* AB-GMRES (Sec. II, Eq. 4): k iterations on A B y = b from y0 = 0 with the
  * basis in data space (k+1 sinogram-size vectors), x = B y.
  * resid[0] = ||b||, resid[j] = ||b - A x_j||.  Arguments as ct_bagmres_solve. */

@@ -292,10 +292,9 @@ __device__ __forceinline__ ColumnView column_view(const GeomDev &g, int s, float
 // a warp's gathers fall on a few neighbouring pixels of a few rows; across
 // it, u moves by M vox/du pixels per lane.  The two partial sums (x-lane
 // views and y-lane views) meet in shared memory.  The sinogram is read as
-// (u, u+1) pairs, one 8-byte load per detector row; the view table sits in
-// shared memory.
+// quads (the 2 x 2 bilinear neighbourhood), one 16-byte load per voxel and
+// view; the view table sits in shared memory.
 constexpr int B_TILE = 32;
-constexpr int B_ZC = 8;
 
 // the four bilinear neighbours of one sinogram quad entry
 template <bool BF>

@@ -135,13 +135,17 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     }
     // back-projector row margin: a voxel at height z projects to row
     // cv + M z/dv with M <= sdd/(sod - r_max); pad so that the floor of that
-    // and the row above stay inside the zero-bordered buffer
+    // and the row above stay inside the zero-bordered buffer, for every
+    // slice the threads compute (runs of B_ZC slices up to a multiple of
+    // B_ZC past nz)
     int padv = PAD_V;
     if (d->kind == CT_CONE_3D) {
         const double vx = d->voxel_mm;
         const double rmax = std::sqrt(std::pow(0.5 * (d->nx - 1) * vx, 2) + std::pow(0.5 * (d->ny - 1) * vx, 2));
         const double mmax = d->sdd_mm / (d->sod_mm - rmax);
-        const double over = 0.5 * (d->nz - 1) * vx * mmax / d->dv_mm - 0.5 * (d->nv - 1);
+        const int nz_run = d->nz == 1 ? 1 : (d->nz + B_ZC - 1) / B_ZC * B_ZC;
+        const double zslices = std::max(0.5 * (d->nz - 1), nz_run - 1 - 0.5 * (d->nz - 1));
+        const double over = zslices * vx * mmax / d->dv_mm - 0.5 * (d->nv - 1);
         padv = std::max(PAD_V, int(std::ceil(std::max(over, 0.0))) + PAD_V);
     }
     // 32-bit indexing of rays, voxels, padded copies and the padded sinogram
@@ -205,12 +209,15 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     // and last plane; every column of every view is visited (the dominant
     // axis switches inside views near 45 degrees).
     //   a_window: 0 <= sigma <= 0.98, so a two-row window per column suffices;
-    //   a_zsafe:  |z| stays within the grid plus one voxel, so no clamp is needed.
+    //   a_zsafe:  |z| stays within the grid plus one voxel, so no clamp is needed;
+    //             checked over the rows the threads compute, which run up to
+    //             the next multiple of A_VR past nv.
     k.a_window = 0;
     k.a_zsafe = 1;
     if (cone) {
         double smin = 1e300, smax = -1e300;
-        const double vmax = 0.5 * (d->nv - 1) * d->dv_mm;
+        const int nv_run = (d->nv + A_VR - 1) / A_VR * A_VR;
+        const double vmax = std::max(0.5 * (d->nv - 1), nv_run - 1 - 0.5 * (d->nv - 1)) * d->dv_mm;
         for (int s = 0; s < d->n_views; ++s) {
             double th = d->angle_start_rad + double(s) * d->angle_span_rad / double(d->n_views);
             double c = std::cos(th), sn = std::sin(th);

@@ -17,6 +17,17 @@ namespace ct {
 constexpr int PAD_A = 2;   // voxels, around the in-plane and z axes of the plane-major copies
 constexpr int PAD_U = 1;   // pixels, both ends of each detector row
 constexpr int PAD_V = 2;   // rows, above and below each view
+// rays per projector thread along a detector column (the last group of a
+// column runs past nv when nv is not a multiple; those rays are discarded)
+#ifndef CT_A_VR
+#define CT_A_VR 8
+#endif
+constexpr int A_VR = CT_A_VR;
+// consecutive z slices per back-projector thread (3D); the last run of a
+// column may pass nz: those slices are computed and discarded, and the
+// padded sinogram's row margin covers them too
+constexpr int B_ZC = 8;
+
 
 // Per-view constants of the projector, from which a ray's direction, its
 // cross product with the source position and the source position follow:

@@ -15,6 +15,8 @@
 // stop, a lucky breakdown or a non-finite norm.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "ct_internal.cuh"
@@ -192,6 +194,33 @@ __device__ __forceinline__ void unpack8(const uint4 w, float (&o)[8])
     o[4] = bf16_lo(w.z); o[5] = bf16_hi(w.z); o[6] = bf16_lo(w.w); o[7] = bf16_hi(w.w);
 }
 
+// One group of 8 elements of the bf16-basis pass: q -= h v_prev (stored
+// back), then the dot with v_cur and the sum of squares of the new q.
+template <int MODE>
+__device__ __forceinline__ void mgs_group8(float4 *q4, float4 lo, float4 hi, uint4 pw, uint4 cw, bool has_prev,
+                                           bool has_cur, bool sumsq, float h, Acc<MODE> &dot, Acc<MODE> &ss)
+{
+    float a[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+    if (has_prev) {
+        float pv[8];
+        unpack8(pw, pv);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) a[e] = fmaf(-h, pv[e], a[e]);
+        q4[0] = make_float4(a[0], a[1], a[2], a[3]);
+        q4[1] = make_float4(a[4], a[5], a[6], a[7]);
+    }
+    if (has_cur) {
+        float cv[8];
+        unpack8(cw, cv);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) dot.add(a[e], cv[e]);
+    }
+    if (sumsq) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) ss.add(a[e], a[e]);
+    }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(RED_BLOCK) mgs_pass_bf16_kernel(
     float *__restrict__ q, const __nv_bfloat16 *__restrict__ vprev, const double *__restrict__ hprev,
@@ -210,28 +239,22 @@ __global__ void __launch_bounds__(RED_BLOCK) mgs_pass_bf16_kernel(
         float4 *q4 = reinterpret_cast<float4 *>(q);
         const uint4 *p8 = reinterpret_cast<const uint4 *>(vprev);
         const uint4 *c8 = reinterpret_cast<const uint4 *>(vcur);
-        for (size_t i = tid; i < n8; i += nth) {
-            const float4 lo = q4[2 * i], hi = q4[2 * i + 1];
-            float a[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-            if (vprev) {
-                float pv[8];
-                unpack8(__ldcs(p8 + i), pv);
-#pragma unroll
-                for (int e = 0; e < 8; ++e) a[e] = fmaf(-h, pv[e], a[e]);
-                q4[2 * i] = make_float4(a[0], a[1], a[2], a[3]);
-                q4[2 * i + 1] = make_float4(a[4], a[5], a[6], a[7]);
-            }
-            if (vcur) {
-                float cv[8];
-                unpack8(__ldcs(c8 + i), cv);
-#pragma unroll
-                for (int e = 0; e < 8; ++e) dot.add(a[e], cv[e]);
-            }
-            if (out_sumsq) {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) ss.add(a[e], a[e]);
-            }
+        const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+        // two groups of 8 per step: all six 16-byte loads are in flight together
+        size_t i = tid;
+        for (; i + nth < n8; i += 2 * nth) {
+            const size_t i1 = i + nth;
+            const float4 l0 = q4[2 * i], h0 = q4[2 * i + 1], l1 = q4[2 * i1], h1 = q4[2 * i1 + 1];
+            const uint4 p0 = vprev ? __ldcs(p8 + i) : zero, p1 = vprev ? __ldcs(p8 + i1) : zero;
+            const uint4 c0 = vcur ? __ldcs(c8 + i) : zero, c1 = vcur ? __ldcs(c8 + i1) : zero;
+            mgs_group8(q4 + 2 * i, l0, h0, p0, c0, vprev != nullptr, vcur != nullptr, out_sumsq != nullptr, h, dot, ss);
+            mgs_group8(q4 + 2 * i1, l1, h1, p1, c1, vprev != nullptr, vcur != nullptr, out_sumsq != nullptr, h, dot,
+                       ss);
         }
+        if (i < n8)
+            mgs_group8(q4 + 2 * i, q4[2 * i], q4[2 * i + 1], vprev ? __ldcs(p8 + i) : zero,
+                       vcur ? __ldcs(c8 + i) : zero, vprev != nullptr, vcur != nullptr, out_sumsq != nullptr, h, dot,
+                       ss);
         start = n8 * 8;
     }
     for (size_t i = start + tid; i < len; i += nth) {
@@ -271,6 +294,32 @@ static unsigned red_blocks(size_t len)
     return unsigned(std::max<size_t>(1, std::min(want, cap)));
 }
 
+// Blocks of a grid-stride pass over len elements (elems per thread-step):
+// every SM gets as many blocks as can be resident at once (at most 8, the
+// size of the partials array), so no partial second wave runs.
+static unsigned resident_blocks(const void *kernel, size_t len, size_t elems)
+{
+    static std::mutex mu;
+    static std::unordered_map<const void *, int> occ;
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = occ.find(kernel);
+        if (it == occ.end()) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, RED_BLOCK, 0) != cudaSuccess) {
+                cudaGetLastError();
+                per_sm = 4;
+            }
+            occ.emplace(kernel, per_sm);
+        } else {
+            per_sm = it->second;
+        }
+    }
+    per_sm = std::min(std::max(per_sm, 1), 8);
+    const size_t want = (len / elems + RED_BLOCK - 1) / RED_BLOCK;
+    return unsigned(std::max<size_t>(1, std::min(want, size_t(num_sms()) * per_sm)));
+}
+
 static size_t partials_count() { return size_t(num_sms()) * 8 * 2; }
 
 static cudaError_t mgs_pass(int mode, float *q, const float *vprev, const double *hprev,
@@ -281,7 +330,9 @@ static cudaError_t mgs_pass(int mode, float *q, const float *vprev, const double
     const int vec4 = (len % 4 == 0) && (reinterpret_cast<uintptr_t>(q) % 16 == 0) &&
                      (!vprev || reinterpret_cast<uintptr_t>(vprev) % 16 == 0) &&
                      (!vcur || reinterpret_cast<uintptr_t>(vcur) % 16 == 0);
-    const unsigned blocks = red_blocks(len);
+    const unsigned blocks = resident_blocks(
+        mode == 0 ? reinterpret_cast<const void *>(mgs_pass_kernel<0>)
+                  : reinterpret_cast<const void *>(mgs_pass_kernel<1>), len, 4);
     ProfScope prof(PK_MGS, st);
     if (mode == 0)
         mgs_pass_kernel<0><<<blocks, RED_BLOCK, 0, st>>>(q, vprev, hprev, vcur, len, vec4, partials,
@@ -304,7 +355,9 @@ static cudaError_t mgs_pass_typed(int mode, bool vbf16, float *q, const void *vp
     const int vec8 = (len % 8 == 0) && (reinterpret_cast<uintptr_t>(q) % 16 == 0) &&
                      (!vprev || reinterpret_cast<uintptr_t>(vprev) % 16 == 0) &&
                      (!vcur || reinterpret_cast<uintptr_t>(vcur) % 16 == 0);
-    const unsigned blocks = red_blocks(len);
+    const unsigned blocks = resident_blocks(
+        mode == 0 ? reinterpret_cast<const void *>(mgs_pass_bf16_kernel<0>)
+                  : reinterpret_cast<const void *>(mgs_pass_bf16_kernel<1>), len, 16);
     ProfScope prof(PK_MGS, st);
     const auto *p = static_cast<const __nv_bfloat16 *>(vprev);
     const auto *c = static_cast<const __nv_bfloat16 *>(vcur);
@@ -1081,6 +1134,37 @@ ct_status ct_bagmres_solve(const ct_geom *geom, const float *b_dev, int k, float
     ct_status rc = check_common(geom, b_dev, k, x_out_dev, &o);
     if (rc != CT_OK) return rc;
     return bagmres(geom, b_dev, k, x_out_dev, resid_hist, o, iters_done, static_cast<cudaStream_t>(stream));
+}
+
+ct_status ct_bagmres_solve_host(const ct_geom *geom, const float *b_host, int k, float *x_out_host,
+                                double *resid_hist, const ct_solve_opts *opts, int *iters_done, void *stream)
+{
+    ct_solve_opts o = resolve_opts(opts);
+    ct_status rc = check_common(geom, b_host, k, x_out_host, &o);
+    if (rc != CT_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t mb = geom->m * sizeof(float), nb = geom->n * sizeof(float);
+    void *bd = nullptr, *xd = nullptr;
+    cudaError_t e = cudaMallocAsync(&bd, mb, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&xd, nb, s);
+    if (e != cudaSuccess) {
+        if (bd) cudaFreeAsync(bd, s);
+        cudaGetLastError();
+        return set_error(CT_ENOMEM, "ct_bagmres_solve_host: device buffers of %zu + %zu bytes: %s", mb, nb,
+                         cudaGetErrorString(e));
+    }
+    e = cudaMemcpyAsync(bd, b_host, mb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        rc = bagmres(geom, static_cast<const float *>(bd), k, static_cast<float *>(xd), resid_hist, o, iters_done, s);
+        if (rc == CT_OK || rc == CT_BREAKDOWN_LUCKY) {
+            e = cudaMemcpyAsync(x_out_host, xd, nb, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+    }
+    cudaFreeAsync(xd, s);
+    cudaFreeAsync(bd, s);
+    if (e != cudaSuccess) return cuda_error(e, "ct_bagmres_solve_host copy");
+    return rc;
 }
 
 ct_status ct_abgmres_solve(const ct_geom *geom, const float *b_dev, int k, float *x_out_dev,

@@ -198,10 +198,7 @@ __device__ __forceinline__ float row_lerp(const float *p, float wb)
     return fmaf(wb, v1 - v0, v0);
 }
 
-// rays per thread along a detector column, and plane-loop unroll (tuning)
-#ifndef CT_A_VR
-#define CT_A_VR 8
-#endif
+// plane-loop unroll (tuning); the rays per thread, A_VR, are in the shared header
 #ifndef CT_A_PUNROLL
 #define CT_A_PUNROLL 2
 #endif

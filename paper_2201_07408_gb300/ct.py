@@ -61,6 +61,7 @@ SIGNATURES = {
     "ct_adjoint_Bt": (_i, [_vp, _vp, _vp, _i, _vp]),
     "ct_ramp_F": (_i, [_vp, _vp, _vp, _i, _vp]),
     "ct_bagmres_solve": (_i, [_vp, _vp, _i, _vp, _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
+    "ct_bagmres_solve_host": (_i, [_vp, _vp, _i, _vp, _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
     "ct_abgmres_solve": (_i, [_vp, _vp, _i, _vp, _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
     "ct_cgls_solve": (_i, [_vp, _vp, _i, _vp, _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
     "ct_bagmres_vjp": (_i, [_vp, _vp, _i, _vp, _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
@@ -126,6 +127,18 @@ def _ptr(t: torch.Tensor, numel: int, name: str, device) -> ctypes.c_void_p:
         raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
     if t.device != device:
         raise ValueError("%s is on %s, the geometry on %s" % (name, t.device, device))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(t: torch.Tensor, numel: int, name: str) -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+        raise TypeError("%s must be a CPU tensor" % name)
+    if t.dtype != torch.float32:
+        raise TypeError("%s must be float32 (got %s)" % (name, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -276,6 +289,27 @@ def ct_bagmres_solve(geom, b, k, x_out, opts=None, stream=None, workspace="torch
     """BA-GMRES, k iterations on B A x = B b (Eq. 5); x_out receives x_k."""
     return _solve("ct_bagmres_solve", lib().ct_bagmres_solve, CT_SOLVER_BA, geom, b, k, x_out, opts, stream,
                   workspace)
+
+
+def ct_bagmres_solve_host(geom, b_host, k, x_out_host, opts=None, stream=None, workspace="torch") -> SolveResult:
+    """BA-GMRES with b and x_k in host memory (CPU float32 tensors; pinned
+    ones give asynchronous copies): copy in, solve, copy out, in one call."""
+    d = geom.device
+    if opts is None:
+        opts = make_opts()
+    if workspace == "torch":
+        nbytes = ct_workspace_bytes(geom, k, CT_SOLVER_BA, opts)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=d)
+        opts.workspace = ctypes.c_void_p(ws.data_ptr())
+        opts.workspace_bytes = nbytes
+    resid = np.zeros(int(k) + 1, dtype=np.float64)
+    iters = ctypes.c_int(0)
+    st = lib().ct_bagmres_solve_host(geom.handle, _host_ptr(b_host, geom.m, "b_host"), int(k),
+                                     _host_ptr(x_out_host, geom.n, "x_out_host"),
+                                     resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opts),
+                                     ctypes.byref(iters), _stream(stream, d))
+    _check("ct_bagmres_solve_host", st, allow=(CT_OK, CT_BREAKDOWN_LUCKY))
+    return SolveResult(status=st, iters=iters.value, resid=resid)
 
 
 def ct_abgmres_solve(geom, b, k, x_out, opts=None, stream=None, workspace="torch") -> SolveResult:

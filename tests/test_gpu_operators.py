@@ -19,7 +19,8 @@ pytestmark = pytest.mark.gpu
 
 OP_TOL = 1e-5
 
-SMALL = [ci.CONE_SMALL, ci.CONE_ANISO, ci.PAR2D_ANISO, ci.PAR2D_64, ci.CONE_GRAD32, ci.CONE_512_CUT64]
+SMALL = [ci.CONE_SMALL, ci.CONE_ANISO, ci.CONE_THIN, ci.PAR2D_ANISO, ci.PAR2D_64, ci.CONE_GRAD32,
+         ci.CONE_512_CUT64]
 
 
 @pytest.fixture(scope="module")

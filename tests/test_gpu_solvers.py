@@ -200,6 +200,24 @@ def test_workspace_and_determinism(ct):
     assert ei.value.status == ct.CT_ENOMEM
 
 
+def test_host_buffer_solve_equals_device_solve(ct):
+    """ct_bagmres_solve_host (b and x in pinned host memory, copies inside
+    the call) runs the same kernels as the device-buffer solve: identical
+    image and residual history."""
+    spec = ci.CONE_ANISO
+    b, _ = data_for(spec)
+    g = ct.Geometry.from_spec(spec)
+    xd = torch.empty(spec.vol_shape, device="cuda")
+    rd = ct.ct_bagmres_solve(g, dev(b), 8, xd, ct.make_opts(b_kind="fbp"))
+    bh = torch.from_numpy(np.ascontiguousarray(b, dtype=np.float32)).pin_memory()
+    xh = torch.full(spec.vol_shape, float("nan")).pin_memory()
+    rh = ct.ct_bagmres_solve_host(g, bh, 8, xh, ct.make_opts(b_kind="fbp"))
+    assert rh.iters == rd.iters == 8
+    assert torch.equal(xh, xd.cpu()) and np.array_equal(rh.resid, rd.resid)
+    with pytest.raises(TypeError):
+        ct.ct_bagmres_solve_host(g, dev(b), 8, xh)
+
+
 def test_reorthogonalisation_keeps_parity(ct):
     spec = ci.CONE_SMALL
     b, _ = data_for(spec)
