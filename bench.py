@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"],
                     help="storage of the working copies and the Krylov basis (arithmetic stays FP32)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="precision sweep at 512^3 (720 views, 768x512 detector), 30 BA-GMRES iterations: "
+                         "FP32 vs BF16 storage x compensated-FP32 vs FP32-FMA dot products; wall time to the "
+                         "FP32 solve's final relative residual")
     ap.add_argument("--op", default=None,
                     choices=["A", "B", "Bfbp", "F", "At", "Bt", "mgs", "ba", "ab", "cgls", "vjp"],
                     help="time one operator, or one whole solve (ba, ab, cgls: --iters iterations with "
@@ -205,10 +209,10 @@ def aggregate_over_ranks(elapsed_s, iters, world, device=None):
 # profiles/.
 NCU_TRAFFIC = {
     # (kernel, storage, workload): (bytes per launch, source file, sha256)
-    ("voxel_B", "f32", "cone_256"): (1416911000 + 68460800, "ct_backproject.cu",
-                                     "7b9ee25c3dcf6eacb3dd60ffb78a49a48378d98654ea43a5d68915322ae668b0"),
-    ("joseph_A", "f32", "cone_256"): (393732352 + 132797696, "ct_project.cu",
-                                      "a7e46fb88ec1cdb0f29666cfb41c9894698e099b53ed0a9defb18fb89d061c23"),
+    ("voxel_B", "f32", "cone_256"): (1419795000 + 68545024, "ct_backproject.cu",
+                                     "598c2b4f8e74d46bcd19646a6b005cf3988ebfd203548784331d0d2136afe45e"),
+    ("joseph_A", "f32", "cone_256"): (393621248 + 132903168, "ct_project.cu",
+                                      "e992b4998bb78646d57771a2aeb270f6188511612edd805398b5d809a3b3acc5"),
 }
 
 
@@ -400,6 +404,17 @@ def run_ours(args, world, rank, local):
                 "gather": {"achieved_gbs": round(gather, 1), "peak_gbs": round(l1_peak, 1),
                            "frac": round(gather / l1_peak, 4),
                            "peak_source": "derived: %d SMs x 128 B/clk x 2070 MHz" % sms}}
+    # semi-convergence (Sec. III, Fig. 4): image error of every iterate
+    # against the true phantom, for B_FBP (the timed solve) and for B_un
+    semi = {}
+    x_tmp = torch.empty_like(x)
+    for kind in ("fbp", "un"):
+        _, err = ct.ct_bagmres_solve_err(g, b, k, x_tmp, x_true_d, ct.make_opts(b_kind=kind))
+        rel_img = err / err[0]
+        jmin = int(np.argmin(np.where(rel_img >= 0, rel_img, np.inf)))
+        semi[kind] = {"min_rel_image_error": round(float(rel_img[jmin]), 5), "at_iter": jmin,
+                      "rel_image_error_at_k": round(float(rel_img[k]), 5)}
+    del x_tmp
     # time to a relative residual of 1e-2 (iterations from the last solve's history)
     hist = res.resid[:res.iters + 1] / res.resid[0]
     hit = np.nonzero(hist <= 1e-2)[0]
@@ -419,7 +434,7 @@ def run_ours(args, world, rank, local):
                              % ((k + 1) * spec.n * 4 / 1e9)},
             "A_gsamples_per_s": round(a_gs, 3), "B_gsamples_per_s": round(b_gs, 3),
             "kernel_ms_per_step": kernel_ms, "resid_final_rel": float(res.resid[res.iters] / res.resid[0]),
-            "time_to_resid_1e-2": ttr,
+            "time_to_resid_1e-2": ttr, "semi_convergence": semi,
             "clocks": clocks, "gpu_launches": int(launches), "roofline": roofline,
             "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": int(spec.m * 4),
                     "d2h_bytes_per_step": int(spec.n * 4 + (k + 1) * 8),
@@ -510,9 +525,57 @@ def run_op(args):
           flush=True)
 
 
+def run_sweep(args):
+    """The storage / reduction precision sweep on the 512^3 scan: one
+    30-iteration BA-GMRES solve (B_FBP, noiseless data of the phantom) per
+    combination, CUDA-event timed; reports each combination's residual
+    history end point, ms per iteration, and the wall time to reach the
+    FP32 / compensated solve's final relative residual."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2201_07408_gb300 import ct
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    spec = ci.CONE_512
+    k = 30
+    x_true = torch.from_numpy(make_inputs(spec)).to(dev)
+    out = []
+    ref_rel = None
+    for storage in ("f32", "bf16"):
+        g = ct.Geometry.from_spec(spec, device=dev, vol_dtype=storage, sino_dtype=storage)
+        b = ct.project_A(g, x_true) if storage == "f32" else b
+        for dot_mode, dot_name in ((0, "compensated FP32, FP64 reduction"), (1, "FP32 FMA, FP64 reduction")):
+            opts = ct.make_opts(b_kind="fbp", dot_mode=dot_mode)
+            x = torch.empty(spec.vol_shape, device=dev)
+            ct.ct_bagmres_solve(g, b, 2, x, ct.make_opts(b_kind="fbp", dot_mode=dot_mode))   # warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            res = ct.ct_bagmres_solve(g, b, k, x, opts)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            rel = res.resid[:res.iters + 1] / res.resid[0]
+            if ref_rel is None:
+                ref_rel = float(rel[-1])
+            hit = np.nonzero(rel <= ref_rel * (1 + 1e-9))[0]
+            out.append({"storage": storage, "dots": dot_name, "iters": res.iters,
+                        "final_rel_resid": float(rel[-1]), "ms_per_iter": round(ms / res.iters, 3),
+                        "iters_to_ref_resid": int(hit[0]) if hit.size else None,
+                        "ms_to_ref_resid": round(float(hit[0]) * ms / res.iters, 1) if hit.size else None})
+            del x
+        g.close()
+    print(json.dumps({"sweep": "precision", "workload": spec.name, "k": k, "b_kind": "fbp",
+                      "ref_rel_resid": ref_rel, "results": out}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.op:
         run_op(args)
         return

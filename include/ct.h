@@ -185,6 +185,39 @@ CT_API ct_status ct_bagmres_solve_host(const ct_geom *geom, const float *b_host,
                                        double *resid_hist, const ct_solve_opts *opts, int *iters_done,
                                        void *stream);
 
+/* ct_bagmres_solve that also measures the image error of every iterate:
+ * err_hist[j] = ||x_j - x_ref|| for j = 0..k (err_hist[0] = ||x_ref||,
+ * since x_0 = 0); entries after the last iteration done are -1.  The
+ * paper's semi-convergence curves (Sec. III, Fig. 4: the image error falls,
+ * reaches a minimum and rises again as the iterates fit the noise) are this
+ * history against the true image.  After the solve each x_j = V_j y_j is
+ * formed in x_out_dev from the first j basis vectors (one pass over them),
+ * so the call costs about k(k+1)/2 extra basis-vector reads; x_out_dev
+ * holds x_k on return.
+ *   x_ref_dev: n floats (device).  err_hist: HOST array of k+1 doubles.
+ * Other arguments and return codes as ct_bagmres_solve. */
+CT_API ct_status ct_bagmres_solve_err(const ct_geom *geom, const float *b_dev, int k, float *x_out_dev,
+                                      const float *x_ref_dev, double *resid_hist, double *err_hist,
+                                      const ct_solve_opts *opts, int *iters_done, void *stream);
+
+/* Restarted BA-GMRES(m) (Sec. II discusses restarting GMRES to bound the
+ * basis): `cycles` cycles of m iterations.  Cycle c solves
+ * B A dx = B (b - A x_c) from dx = 0 with m BA-GMRES iterations (the basis
+ * holds m+1 vectors) and sets x_{c+1} = x_c + dx; x_0 = 0.
+ *   resid_hist: HOST array of m*cycles + 1 doubles: resid[0] = ||B b||,
+ *               then the m residuals ||B (b - A x)|| of each cycle in turn;
+ *               -1 after the last iteration done.  May be NULL.
+ *   iters_done: total iterations over all cycles.
+ * opts->tol stops a cycle at tol times that cycle's starting residual and
+ * stops the solve when the residual reaches tol times resid[0].  Scratch
+ * (the projector's copies, two sinograms and one volume) comes from the
+ * stream-ordered allocator; the workspace, when given, is as for
+ * ct_bagmres_solve with k = m.  Synchronous.  Return codes as
+ * ct_bagmres_solve; CT_EINVAL for cycles < 1. */
+CT_API ct_status ct_bagmres_restarted(const ct_geom *geom, const float *b_dev, int m, int cycles,
+                                      float *x_out_dev, double *resid_hist, const ct_solve_opts *opts,
+                                      int *iters_done, void *stream);
+
 /* AB-GMRES (Sec. II, Eq. 4): k iterations on A B y = b from y0 = 0 with the
  * basis in data space (k+1 sinogram-size vectors), x = B y.
  * resid[0] = ||b||, resid[j] = ||b - A x_j||.  Arguments as ct_bagmres_solve. */

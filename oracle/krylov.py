@@ -121,6 +121,29 @@ def ba_gmres(A, B, b, k, keep_basis=True):
     return out
 
 
+def ba_gmres_restarted(A, B, b, m, cycles):
+    """Restarted BA-GMRES(m) (Sec. II): cycle c runs m BA-GMRES iterations on
+    B A dx = B (b - A x_c) from dx = 0 and sets x_{c+1} = x_c + dx, x_0 = 0.
+
+    Returns dict(x_final, resid) with resid[0] = ||B b|| followed by each
+    cycle's residuals ||B (b - A x)|| after its iterations 1..m; a cycle
+    that ends early (lucky breakdown) ends the solve."""
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    x = None
+    resid = []
+    for c in range(cycles):
+        r = b if x is None else b - np.asarray(A(x)).reshape(-1)
+        out = ba_gmres(A, B, r, m, keep_basis=False)
+        dx = out["x_final"]
+        x = dx if x is None else x + dx
+        if c == 0:
+            resid.append(out["resid"][0])
+        resid.extend(out["resid"][1:])
+        if out["iters"] < m:
+            break
+    return dict(x_final=x, resid=np.array(resid))
+
+
 def ab_gmres(A, B, b, k, keep_basis=True):
     """AB-GMRES (Eq. 4): minimise ||A B y - b|| over y in K_j(AB, b); x = B y."""
     b = np.asarray(b, dtype=np.float64).reshape(-1)

@@ -77,55 +77,6 @@ cudaError_t launch_pad_sino(const GeomDev &g, float *src, const double *scale, b
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Ramp filter.  The Ram-Lak kernel is zero at even nonzero offsets, so each
-// output parity only sees samples of the other parity:
-//   out[2i]   = h0 E[i] + sum_m g[m] (O[i-m-1] + O[i+m])
-//   out[2i+1] = h0 O[i] + sum_m g[m] (E[i-m]   + E[i+m+1])
-// with E, O the even / odd samples of the (cosine-weighted) row and
-// g[m] = h[2m+1].  A thread computes RAMP_R consecutive outputs of one
-// parity for two detector rows at once: the two rows are interleaved in
-// shared memory (float2), so each tap costs two 8-byte shared loads and
-// RAMP_R packed FADD2/FFMA2 for 2*RAMP_R outputs.  The two register windows
-// slide by one sample per tap as ring buffers whose slot indices are
-// compile-time constants (the tap loop is unrolled by RAMP_R and the tap
-// count padded with zero taps), so sliding costs no moves.  RAMP_R is odd
-// so that the window loads of neighbouring threads fall in distinct banks.
-// Rows sit in shared memory with zero margins, so no load is bounds-tested.
-// F^T weights the output instead of the input.
-// ---------------------------------------------------------------------------
-constexpr int RAMP_R = 9;
-
-struct RampShape {
-    int M;       // taps g[0..M-1], M a multiple of RAMP_R (zero taps past nu/2)
-    int mpad;    // floats reserved for the taps: M rounded up to 4, so the float2 rows start 16-byte aligned
-    int nhE, nhO;
-    int off;     // index of sample 0 inside a half-row array
-    int len;     // length of one half-row array (float2 entries)
-    int tpr;     // threads per row pair
-    int pairs;   // row pairs per block
-    int threads;
-    size_t smem;
-};
-
-static RampShape ramp_shape(int nu)
-{
-    RampShape r;
-    const int mtaps = nu / 2;
-    r.M = ((mtaps + RAMP_R - 1) / RAMP_R) * RAMP_R;
-    if (r.M == 0) r.M = RAMP_R;
-    r.nhE = (nu + 1) / 2;
-    r.nhO = nu / 2;
-    r.off = r.M + 1;
-    r.len = r.off + r.nhE + RAMP_R + r.M + 2;
-    r.tpr = (r.nhE + RAMP_R - 1) / RAMP_R + (r.nhO + RAMP_R - 1) / RAMP_R;
-    r.pairs = r.tpr >= 256 ? 1 : 256 / r.tpr;
-    r.threads = ((r.tpr * r.pairs + 31) / 32) * 32;
-    r.mpad = (r.M + 3) & ~3;
-    r.smem = sizeof(float) * size_t(r.mpad) + sizeof(float2) * size_t(r.pairs) * 2 * r.len;
-    return r;
-}
-
 __device__ __forceinline__ float cosine_weight(const GeomDev &g, int iu, int iv)
 {
     if (g.kind != CT_CONE_3D) return 1.0f;
@@ -134,109 +85,226 @@ __device__ __forceinline__ float cosine_weight(const GeomDev &g, int iu, int iv)
     return g.sdd / sqrtf(fmaf(g.sdd, g.sdd, fmaf(u, u, v * v)));
 }
 
-__device__ __forceinline__ int ring(int x) { return ((x % RAMP_R) + RAMP_R) % RAMP_R; }
-
-// acc[j] = h0 C[i0+j] + sum_m g[m] (L[i0+j-m-AL] + L[i0+j+m+AR]) for two rows at once
-template <int AL, int AR>
-__device__ __forceinline__ void ramp_conv(const float2 *__restrict__ L, const float2 *__restrict__ C,
-                                          const float *__restrict__ gm, int M, int i0, float h0,
-                                          float2 (&acc)[RAMP_R])
+// ---------------------------------------------------------------------------
+// Ramp filter by FFT.  Two detector rows are filtered at once as the real
+// and imaginary parts of one complex row z = x1 + i x2, zero-padded to
+// N = fft_n: the kernel's spectrum H is real, so the inverse transform of
+// H FFT(z) is (h * x1) + i (h * x2), the two linear convolutions (N is at
+// least 2 nu - 1, so the circular wrap misses the first nu outputs).  The
+// inverse is taken as a forward transform of the conjugate,
+// IFFT(Y) = conj(FFT(conj(Y))) / N, with 1/N folded into H.
+//
+// The transform is a Stockham autosort FFT in shared memory, radix 4 (a
+// radix-2 stage last when N is not a power of 4), output in natural order.
+// A stage of radix R after Ns points have been combined: butterfly j reads
+// element j + r N/R (r < R), multiplies it by exp(-2 pi i r (j mod Ns) /
+// (R Ns)), transforms the R values and writes value r to
+// (j - j mod Ns) R + j mod Ns + r Ns.
+//
+// A group of N/4 threads owns one row pair; a block runs 256/(N/4) groups
+// (one group of N/4 threads when N > 1024) and loops over row pairs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
-    // ring slots: left element q = i0 + j - m - AL sits in slot ring(q - i0),
-    // right element q = i0 + j + m + AR in slot ring(q - i0)
-    float2 Lw[RAMP_R], Rw[RAMP_R];
-#pragma unroll
-    for (int j = 0; j < RAMP_R; ++j) {   // state before tap 0 (m = -1)
-        Lw[ring(j + 1 - AL)] = L[i0 + j + 1 - AL];
-        Rw[ring(j - 1 + AR)] = L[i0 + j - 1 + AR];
-        const float2 c = C[i0 + j];
-        acc[j] = make_float2(h0 * c.x, h0 * c.y);
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// Twiddles in shared memory, stage by stage: the radix-4 stage that follows
+// Ns combined points uses exp(-2 pi i r k / (4 Ns)), r = 1..3, k < Ns, stored
+// at stw[(Ns - 1) + (r - 1) Ns + k] (stages Ns = 1, 4, 16, ... take 3 Ns
+// entries each, starting at Ns - 1 = 4^s - 1); the radix-2 stage's
+// exp(-2 pi i k / N), k < N/2, follow.  Lanes with consecutive k read
+// consecutive entries (in the full-length table they are N/(4 Ns) entries
+// apart, all in one bank).
+__device__ __forceinline__ int fft_stage_table(int N)
+{
+    int Ns = 1;
+    while (Ns * 4 <= N) Ns *= 4;
+    return Ns - 1;   // radix-4 entries: the sum over the stages of 3 Ns
+}
+
+// Buffer element i lives at slot fsw(i): within each aligned block of 16
+// elements the low four bits are XORed with 5 ((i >> 4) mod 4).  The
+// radix-4 stages after 1 and 4 combined points write elements 4t + r and
+// 16 (t div 4) + (t mod 4) + 4r; unswizzled, 16 lanes of a shared-memory
+// phase then hit only 4 of the 16 eight-byte banks.  The swizzle spreads
+// both patterns over all 16 and keeps runs of consecutive elements (every
+// other access) on distinct banks.
+__device__ __forceinline__ int fsw(int i) { return i ^ (5 * ((i >> 4) & 3)); }
+
+// One FFT of length N (= 4 T) by the T threads of a group; a holds the input
+// and receives the output, b is scratch.  Every thread of the block calls it
+// (it synchronises the block).
+__device__ __forceinline__ void fft_group(float2 *&a, float2 *&b, const float2 *__restrict__ stw, int N, int t)
+{
+    const int T = N >> 2;
+    int Ns = 1;
+    for (; Ns * 4 <= N; Ns *= 4) {
+        const int k = t & (Ns - 1);
+        float2 v0 = a[fsw(t)], v1 = a[fsw(t + T)], v2 = a[fsw(t + 2 * T)], v3 = a[fsw(t + 3 * T)];
+        if (Ns > 1) {
+            const float2 *w = stw + (Ns - 1) + k;
+            v1 = cmul(v1, w[0]);
+            v2 = cmul(v2, w[Ns]);
+            v3 = cmul(v3, w[2 * Ns]);
+        }
+        const float2 s02 = make_float2(v0.x + v2.x, v0.y + v2.y), d02 = make_float2(v0.x - v2.x, v0.y - v2.y);
+        const float2 s13 = make_float2(v1.x + v3.x, v1.y + v3.y), d13 = make_float2(v1.x - v3.x, v1.y - v3.y);
+        const int d = ((t - k) << 2) + k;
+        b[fsw(d)] = make_float2(s02.x + s13.x, s02.y + s13.y);
+        b[fsw(d + Ns)] = make_float2(d02.x + d13.y, d02.y - d13.x);       // d02 - i d13
+        b[fsw(d + 2 * Ns)] = make_float2(s02.x - s13.x, s02.y - s13.y);
+        b[fsw(d + 3 * Ns)] = make_float2(d02.x - d13.y, d02.y + d13.x);   // d02 + i d13
+        __syncthreads();
+        float2 *tmp = a;
+        a = b;
+        b = tmp;
     }
-    for (int m0 = 0; m0 < M; m0 += RAMP_R) {
+    if (Ns < N) {   // N = 2 Ns: one radix-2 stage, two butterflies per thread
+        const float2 *w2 = stw + (Ns - 1);
 #pragma unroll
-        for (int t = 0; t < RAMP_R; ++t) {
-            const int m = m0 + t;
-            Lw[ring(-t - AL)] = L[i0 - m - AL];                 // enters at j = 0
-            Rw[ring(RAMP_R - 1 + t + AR)] = L[i0 + RAMP_R - 1 + m + AR];   // enters at j = R-1
-            const float gv = gm[m];
-            const float2 g2 = make_float2(gv, gv);
-#pragma unroll
-            for (int j = 0; j < RAMP_R; ++j)
-                acc[j] = __ffma2_rn(g2, __fadd2_rn(Lw[ring(j - t - AL)], Rw[ring(j + t + AR)]), acc[j]);
+        for (int h = 0; h < 2; ++h) {
+            const int j = t + h * T;
+            const int k = j & (Ns - 1);
+            const float2 v0 = a[fsw(j)], v1 = cmul(a[fsw(j + N / 2)], w2[k]);
+            const int d = ((j - k) << 1) + k;
+            b[fsw(d)] = make_float2(v0.x + v1.x, v0.y + v1.y);
+            b[fsw(d + Ns)] = make_float2(v0.x - v1.x, v0.y - v1.y);
+        }
+        __syncthreads();
+        float2 *tmp = a;
+        a = b;
+        b = tmp;
+    }
+}
+
+struct FftShape {
+    int T;        // threads per group (N / 4)
+    int groups;   // row pairs per block at a time
+    int threads;
+    size_t smem;
+};
+
+static FftShape fft_shape(int N)
+{
+    FftShape f;
+    f.T = N / 4;
+    f.groups = f.T >= 256 ? 1 : 256 / f.T;
+    f.threads = f.T * f.groups;
+    // staged twiddles (< 3N/2), spectrum (N floats), two buffers per group
+    f.smem = sizeof(float2) * size_t(3 * N / 2) + sizeof(float) * size_t(N) + sizeof(float2) * 2 * size_t(N) * f.groups;
+    return f;
+}
+
+__global__ void ramp_fft_kernel(GeomDev g, const float *__restrict__ src, float *__restrict__ dst, SinoLayout lay,
+                                int transpose, const int *__restrict__ stop)
+{
+    if (stop && *stop) return;
+    extern __shared__ float2 fsm[];
+    const int N = g.fft_n, T = N >> 2;
+    const int groups = blockDim.x / T;
+    float2 *stw = fsm;                                              // staged twiddles, < 3N/2
+    float *H = reinterpret_cast<float *>(fsm + 3 * N / 2);         // N spectrum values / N
+    const int grp = threadIdx.x / T, t = threadIdx.x - grp * T;
+    float2 *a = fsm + 2 * N + size_t(grp) * 2 * N;                 // this group's two buffers
+    float2 *b = a + N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) H[i] = g.fft_h[i];
+    for (int Ns = 1; Ns * 4 <= N; Ns *= 4)   // radix-4 entries (Ns - 1) + (r - 1) Ns + k = tw[r k N / (4 Ns)]
+        for (int i = threadIdx.x; i < 3 * Ns; i += blockDim.x) {
+            const int r = i / Ns + 1, k = i - (r - 1) * Ns;
+            stw[(Ns - 1) + i] = g.fft_tw[r * k * (N / (4 * Ns))];
+        }
+    {
+        const int r4 = fft_stage_table(N);
+        if (r4 + 1 < N)   // a radix-2 stage (Ns = N / 2) follows: tw[k], k < N / 2
+            for (int i = threadIdx.x; i < N / 2; i += blockDim.x) stw[r4 + i] = g.fft_tw[i];
+    }
+    const int nu = g.nu;
+    const int nrows = g.n_views * g.nv;
+    const int npairs = (nrows + 1) / 2;
+    for (int base = blockIdx.x * groups; base < npairs; base += gridDim.x * groups) {
+        const int pr = base + grp;
+        const bool live = pr < npairs;
+        const int r0 = 2 * pr, r1 = 2 * pr + 1;
+        const bool has1 = live && r1 < nrows;
+        const int s0 = r0 / g.nv, iv0 = r0 - s0 * g.nv;
+        const int s1 = r1 / g.nv, iv1 = r1 - s1 * g.nv;
+        __syncthreads();   // the previous pair's output reads are done (and the tables are in)
+        for (int u = t; u < N; u += T) {
+            float2 z = make_float2(0.0f, 0.0f);
+            if (live && u < nu) {
+                z.x = src[size_t(r0) * nu + u];
+                if (has1) z.y = src[size_t(r1) * nu + u];
+                if (!transpose) {
+                    z.x *= cosine_weight(g, u, iv0);
+                    z.y *= cosine_weight(g, u, iv1);
+                }
+            }
+            a[fsw(u)] = z;
+        }
+        __syncthreads();
+        fft_group(a, b, stw, N, t);
+        for (int k = t; k < N; k += T) {   // conj(Z) H / N
+            const float2 z = a[fsw(k)];
+            a[fsw(k)] = make_float2(z.x * H[k], -z.y * H[k]);
+        }
+        __syncthreads();
+        fft_group(a, b, stw, N, t);
+        // conj of the transform: row 0 in .x, row 1 in -.y
+        if (live && lay.quads) {
+            // horizontal pairs (u, u+1) for u = -1 .. nu-1, two 8-byte stores each
+            for (int u = t - 1; u < nu; u += T) {
+                float l0 = 0.0f, h0 = 0.0f, l1 = 0.0f, h1 = 0.0f;
+                if (u >= 0) {
+                    const float2 y = a[fsw(u)];
+                    l0 = transpose ? y.x * cosine_weight(g, u, iv0) : y.x;
+                    l1 = transpose ? -y.y * cosine_weight(g, u, iv1) : -y.y;
+                }
+                if (u + 1 < nu) {
+                    const float2 y = a[fsw(u + 1)];
+                    h0 = transpose ? y.x * cosine_weight(g, u + 1, iv0) : y.x;
+                    h1 = transpose ? -y.y * cosine_weight(g, u + 1, iv1) : -y.y;
+                }
+                store_sino_pair(dst, lay, s0, iv0, u, l0, h0);
+                if (has1) store_sino_pair(dst, lay, s1, iv1, u, l1, h1);
+            }
+        } else if (live) {
+            for (int u = t; u < nu; u += T) {
+                const float2 y = a[fsw(u)];
+                store_sino(dst, lay, s0, iv0, u, transpose ? y.x * cosine_weight(g, u, iv0) : y.x);
+                if (has1) store_sino(dst, lay, s1, iv1, u, transpose ? -y.y * cosine_weight(g, u, iv1) : -y.y);
+            }
         }
     }
 }
 
-__global__ void ramp_kernel(GeomDev g, RampShape rs, const float *__restrict__ src, float *__restrict__ dst,
-                            SinoLayout lay, int transpose, const int *__restrict__ stop)
+static cudaError_t launch_ramp_fft(const GeomDev &g, const float *src, float *dst, SinoLayout lay, bool transpose,
+                                   const int *stop, cudaStream_t st)
 {
-    if (stop && *stop) return;
-    extern __shared__ float sm[];
-    const int nu = g.nu;
-    const int nrows = g.n_views * g.nv;
-    float *gm = sm;                                                 // taps g[m] = h[2m+1]
-    float2 *half = reinterpret_cast<float2 *>(sm + rs.mpad);        // [pair][E | O][len]
-    const int row_base = blockIdx.x * rs.pairs * 2;
-    for (int i = threadIdx.x; i < rs.M; i += blockDim.x) gm[i] = 2 * i + 1 < nu ? g.ramp_taps[2 * i + 1] : 0.0f;
-    for (int i = threadIdx.x; i < rs.pairs * 2 * rs.len; i += blockDim.x) half[i] = make_float2(0.0f, 0.0f);
-    __syncthreads();
-    float *halff = reinterpret_cast<float *>(half);
-    for (int i = threadIdx.x; i < rs.pairs * 2 * nu; i += blockDim.x) {
-        const int lr = i / nu, iu = i - lr * nu;     // lr: row within the block
-        const int r = row_base + lr;
-        if (r >= nrows) continue;
-        const int iv = r % g.nv;
-        const float w = transpose ? 1.0f : cosine_weight(g, iu, iv);
-        const int pair = lr >> 1, comp = lr & 1;
-        const size_t e = (size_t(pair) * 2 + (iu & 1)) * rs.len + rs.off + (iu >> 1);
-        halff[2 * e + comp] = src[size_t(r) * nu + iu] * w;
+    const FftShape fs = fft_shape(g.fft_n);
+    if (fs.smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(ramp_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(fs.smem));
+        if (e != cudaSuccess) return e;
     }
-    __syncthreads();
-    const int lp = threadIdx.x / rs.tpr;
-    const int tile = threadIdx.x - lp * rs.tpr;
-    const int r0 = row_base + 2 * lp;
-    if (lp >= rs.pairs || r0 >= nrows) return;
-    const float2 *E = half + size_t(lp) * 2 * rs.len + rs.off;
-    const float2 *O = E + rs.len;
-    const int tilesE = (rs.nhE + RAMP_R - 1) / RAMP_R;
-    const int parity = tile < tilesE ? 0 : 1;
-    const int i0 = (parity ? tile - tilesE : tile) * RAMP_R;
-    const float h0 = g.ramp_taps[0];
-    float2 acc[RAMP_R];
-    if (parity == 0)
-        ramp_conv<1, 0>(O, E, gm, rs.M, i0, h0, acc);
-    else
-        ramp_conv<0, 1>(E, O, gm, rs.M, i0, h0, acc);
-    const int nh = parity ? rs.nhO : rs.nhE;
-    const bool second = r0 + 1 < nrows;
-    const int iv0 = r0 % g.nv, s0 = r0 / g.nv;
-    const int iv1 = (r0 + 1) % g.nv, s1 = (r0 + 1) / g.nv;
-#pragma unroll
-    for (int j = 0; j < RAMP_R; ++j) {
-        const int i = i0 + j;
-        if (i < nh) {
-            const int iu = 2 * i + parity;
-            store_sino(dst, lay, s0, iv0, iu, transpose ? acc[j].x * cosine_weight(g, iu, iv0) : acc[j].x);
-            if (second)
-                store_sino(dst, lay, s1, iv1, iu, transpose ? acc[j].y * cosine_weight(g, iu, iv1) : acc[j].y);
-        }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ramp_fft_kernel, fs.threads, fs.smem) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
     }
+    const int npairs = (g.n_views * g.nv + 1) / 2;
+    const int want = (npairs + fs.groups - 1) / fs.groups;
+    const unsigned blocks = unsigned(std::max(1, std::min(want, num_sms() * per_sm)));
+    ProfScope prof(PK_RAMP, st);
+    ramp_fft_kernel<<<blocks, fs.threads, fs.smem, st>>>(g, src, dst, lay, transpose ? 1 : 0, stop);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ramp(const GeomDev &g, const float *src, float *dst, SinoLayout lay, bool transpose,
                         const int *stop, cudaStream_t st)
 {
-    const RampShape rs = ramp_shape(g.nu);
-    if (rs.smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(ramp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(rs.smem));
-        if (e != cudaSuccess) return e;
-    }
-    const int nrows = g.n_views * g.nv;
-    const unsigned blocks = unsigned((nrows + 2 * rs.pairs - 1) / (2 * rs.pairs));
-    ProfScope prof(PK_RAMP, st);
-    ramp_kernel<<<blocks, rs.threads, rs.smem, st>>>(g, rs, src, dst, lay, transpose ? 1 : 0, stop);
-    return cudaGetLastError();
+    return launch_ramp_fft(g, src, dst, lay, transpose, stop, st);
 }
 
 // ---------------------------------------------------------------------------

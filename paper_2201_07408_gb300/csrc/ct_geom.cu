@@ -242,6 +242,7 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     // Ram-Lak taps of the ramp filter with the FBP scale folded in:
     // h[0] = 1/(4 tau^2), h[odd k] = -1/(pi^2 k^2 tau^2), h[even k] = 0, times tau * c_F.
     std::vector<float> taps(d->nu);
+    std::vector<double> taps64(d->nu);
     {
         const double PI = 3.14159265358979323846;
         double tau = cone ? d->du_mm * d->sod_mm / d->sdd_mm : d->du_mm;
@@ -253,13 +254,37 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         for (int q = 0; q < d->nu; ++q) {
             double h = q == 0 ? 1.0 / (4.0 * tau * tau)
                               : (q % 2 ? -1.0 / (PI * PI * double(q) * q * tau * tau) : 0.0);
+            taps64[q] = h * scale;
             taps[q] = float(h * scale);
+        }
+    }
+    // the same kernel as a spectrum: circular convolution of length N with
+    // the kernel wrapped (h[q] at q and N - q) equals the linear one on the
+    // first nu outputs when N >= 2 nu - 1; h is even, so H is real:
+    //   H[k] = h[0] + 2 sum_{q >= 1} h[q] cos(2 pi q k / N)
+    int fft_n = 8;
+    while (fft_n < 2 * d->nu - 1) fft_n *= 2;
+    std::vector<float2> fft_tw(fft_n);
+    std::vector<float> fft_h(fft_n);
+    {
+        const double PI = 3.14159265358979323846;
+        std::vector<double> cs(fft_n);
+        for (int t = 0; t < fft_n; ++t) {
+            cs[t] = std::cos(2.0 * PI * t / fft_n);
+            fft_tw[t] = make_float2(float(cs[t]), float(-std::sin(2.0 * PI * t / fft_n)));
+        }
+        for (int kk = 0; kk < fft_n; ++kk) {
+            double acc = taps64[0];
+            for (int q = 1; q < d->nu; ++q) acc += 2.0 * taps64[q] * cs[size_t(q) * kk % fft_n];
+            fft_h[kk] = float(acc / fft_n);
         }
     }
     size_t bA = Arena::align(va.size() * sizeof(ViewA));
     size_t bB = Arena::align(vb.size() * sizeof(ViewB));
     size_t bT = Arena::align(taps.size() * sizeof(float));
-    cudaError_t e = cudaMalloc(&g->d_tables, bA + bB + bT);
+    size_t bW = Arena::align(fft_tw.size() * sizeof(float2));
+    size_t bH = Arena::align(fft_h.size() * sizeof(float));
+    cudaError_t e = cudaMalloc(&g->d_tables, bA + bB + bT + bW + bH);
     if (e != cudaSuccess) {
         delete g;
         return cuda_error(e, "cudaMalloc(geometry tables)");
@@ -270,6 +295,10 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         e = cudaMemcpy(base + bA, vb.data(), vb.size() * sizeof(ViewB), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(base + bA + bB, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(base + bA + bB + bT, fft_tw.data(), fft_tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(base + bA + bB + bT + bW, fft_h.data(), fft_h.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(g->d_tables);
         delete g;
@@ -278,6 +307,9 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     k.viewA = reinterpret_cast<const ViewA *>(base);
     k.viewB = reinterpret_cast<const ViewB *>(base + bA);
     k.ramp_taps = reinterpret_cast<const float *>(base + bA + bB);
+    k.fft_n = fft_n;
+    k.fft_tw = reinterpret_cast<const float2 *>(base + bA + bB + bT);
+    k.fft_h = reinterpret_cast<const float *>(base + bA + bB + bT + bW);
     *out = g;
     return CT_OK;
 }

@@ -26,7 +26,10 @@ constexpr int A_VR = CT_A_VR;
 // consecutive z slices per back-projector thread (3D); the last run of a
 // column may pass nz: those slices are computed and discarded, and the
 // padded sinogram's row margin covers them too
-constexpr int B_ZC = 8;
+#ifndef CT_B_ZC
+#define CT_B_ZC 8
+#endif
+constexpr int B_ZC = CT_B_ZC;
 
 
 // Per-view constants of the projector, from which a ray's direction, its
@@ -79,6 +82,14 @@ struct GeomDev {
     //              and the BA-GMRES Krylov basis is bf16;
     //   sino_bf16: the back-projector's quad sinogram holds 4 bf16 (8 bytes).
     int vol_bf16, sino_bf16;
+    // ramp filter by FFT: the linear convolution of a row with the ramp
+    // kernel is the circular one of length fft_n >= 2 nu - 1 (a power of
+    // two); the kernel is even, so its spectrum is real.
+    //   fft_tw[t] = exp(-2 pi i t / fft_n), t < fft_n
+    //   fft_h[k]  = spectrum of the scaled kernel / fft_n, k < fft_n
+    int fft_n;
+    const float2 *fft_tw;
+    const float *fft_h;
 };
 
 // Layout of a sinogram buffer that an operator writes.
@@ -184,6 +195,27 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&p);
 }
 
+// Stores the horizontal pair (S[v][u], S[v][u+1]) of a quad-layout
+// sinogram: it is the first half of entry (v, u) and the second half of
+// entry (v-1, u), one 8-byte (4-byte for bf16) store each.  u may be -1
+// (S[v][-1] = 0): the padded layout has that column.
+__device__ __forceinline__ void store_sino_pair(float *out, const SinoLayout &lay, int s, int iv, int iu, float lo,
+                                                float hi)
+{
+    const size_t e = (size_t(s) * lay.rows_per_view + iv + lay.row_off) * lay.pitch + iu + lay.col_off;
+    const size_t up = e - lay.pitch;
+    if (lay.bf16) {
+        uint32_t *o = reinterpret_cast<uint32_t *>(out);
+        const uint32_t w = pack_bf16x2(lo, hi);
+        o[2 * e] = w;
+        o[2 * up + 1] = w;
+    } else {
+        float2 *o = reinterpret_cast<float2 *>(out);
+        o[2 * e] = make_float2(lo, hi);
+        o[2 * up + 1] = make_float2(lo, hi);
+    }
+}
+
 // --- projector (ct_project.cu) ---------------------------------------------------
 // Builds the plane-major zero-bordered copies Xc, Yc (float, or bf16 pairs
 // when g.vol_bf16) of the volume `vol` scaled by (*scale) when scale !=
@@ -194,8 +226,9 @@ cudaError_t launch_plane_copies(const GeomDev &g, const float *vol, const double
 // y = A x from the plane copies, written in `lay`.
 cudaError_t launch_joseph_A(const GeomDev &g, const float *Xc, const float *Yc, float *y,
                             SinoLayout lay, const int *stop, cudaStream_t st);
-// x += A^T y (x must be zeroed by the caller); y in plain layout.
-cudaError_t launch_joseph_At(const GeomDev &g, const float *y, float *x, const int *stop,
+// x = A^T y (overwritten); y in plain layout.  Xa, Ya: accumulators of the
+// projector's copy sizes (contents overwritten).
+cudaError_t launch_joseph_At(const GeomDev &g, const float *y, float *x, float *Xa, float *Ya, const int *stop,
                              cudaStream_t st);
 
 // --- back-projector (ct_backproject.cu) ------------------------------------------

@@ -130,6 +130,33 @@ __device__ __forceinline__ void grid_finish(double a, double b, double *partials
 // One MGS pass: q -= (*hprev) vprev (if vprev), then <q, vcur> (if vcur) and
 // ||q||^2 (if out_sumsq).  Stops early on *stop, or on *skip when given.
 // ---------------------------------------------------------------------------
+// One group of 4 elements of the FP32 pass: q -= h v_prev (stored back),
+// then the dot with v_cur and the sum of squares of the new q.
+template <int MODE>
+__device__ __forceinline__ void mgs_group4(float4 *q4, float4 a, float4 p, float4 c, bool has_prev, bool has_cur,
+                                           bool sumsq, float h, Acc<MODE> &dot, Acc<MODE> &ss)
+{
+    if (has_prev) {
+        a.x = fmaf(-h, p.x, a.x);
+        a.y = fmaf(-h, p.y, a.y);
+        a.z = fmaf(-h, p.z, a.z);
+        a.w = fmaf(-h, p.w, a.w);
+        *q4 = a;
+    }
+    if (has_cur) {
+        dot.add(a.x, c.x);
+        dot.add(a.y, c.y);
+        dot.add(a.z, c.z);
+        dot.add(a.w, c.w);
+    }
+    if (sumsq) {
+        ss.add(a.x, a.x);
+        ss.add(a.y, a.y);
+        ss.add(a.z, a.z);
+        ss.add(a.w, a.w);
+    }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(RED_BLOCK) mgs_pass_kernel(
     float *__restrict__ q, const float *__restrict__ vprev, const double *__restrict__ hprev,
@@ -148,30 +175,21 @@ __global__ void __launch_bounds__(RED_BLOCK) mgs_pass_kernel(
         float4 *q4 = reinterpret_cast<float4 *>(q);
         const float4 *p4 = reinterpret_cast<const float4 *>(vprev);
         const float4 *c4 = reinterpret_cast<const float4 *>(vcur);
-        for (size_t i = tid; i < n4; i += nth) {
-            float4 a = q4[i];
-            if (vprev) {
-                const float4 p = __ldcs(p4 + i);   // basis vectors stream through L2 (evict first)
-                a.x = fmaf(-h, p.x, a.x);
-                a.y = fmaf(-h, p.y, a.y);
-                a.z = fmaf(-h, p.z, a.z);
-                a.w = fmaf(-h, p.w, a.w);
-                q4[i] = a;
-            }
-            if (vcur) {
-                const float4 c = __ldcs(c4 + i);
-                dot.add(a.x, c.x);
-                dot.add(a.y, c.y);
-                dot.add(a.z, c.z);
-                dot.add(a.w, c.w);
-            }
-            if (out_sumsq) {
-                ss.add(a.x, a.x);
-                ss.add(a.y, a.y);
-                ss.add(a.z, a.z);
-                ss.add(a.w, a.w);
-            }
+        const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        // two groups of 4 per step: the six 16-byte loads are in flight together
+        // (basis vectors stream through L2 evict-first)
+        size_t i = tid;
+        for (; i + nth < n4; i += 2 * nth) {
+            const size_t i1 = i + nth;
+            const float4 a0 = q4[i], a1 = q4[i1];
+            const float4 p0 = vprev ? __ldcs(p4 + i) : zero, p1 = vprev ? __ldcs(p4 + i1) : zero;
+            const float4 c0 = vcur ? __ldcs(c4 + i) : zero, c1 = vcur ? __ldcs(c4 + i1) : zero;
+            mgs_group4(q4 + i, a0, p0, c0, vprev != nullptr, vcur != nullptr, out_sumsq != nullptr, h, dot, ss);
+            mgs_group4(q4 + i1, a1, p1, c1, vprev != nullptr, vcur != nullptr, out_sumsq != nullptr, h, dot, ss);
         }
+        if (i < n4)
+            mgs_group4(q4 + i, q4[i], vprev ? __ldcs(p4 + i) : zero, vcur ? __ldcs(c4 + i) : zero, vprev != nullptr,
+                       vcur != nullptr, out_sumsq != nullptr, h, dot, ss);
         start = n4 * 4;
     }
     for (size_t i = start + tid; i < len; i += nth) {
@@ -453,6 +471,30 @@ __global__ void givens_kernel(int j, int k, double *H, const double *H2, double 
     }
 }
 
+// *cnt = j when iterate j exists (j <= iterations done), else 0
+__global__ void iterate_count_kernel(const SolverState *st, int j, int *cnt) { *cnt = j <= st->iters ? j : 0; }
+
+// y = R_j^{-1} g_j for the first *cnt columns: the least-squares coefficients
+// of iterate x_j (R's first j columns and g's first j entries are final once
+// iteration j is done)
+__global__ void backsolve_count_kernel(const double *R, const double *g, double *y, const int *cnt, int k)
+{
+    const int it = *cnt;
+    const int ld = k + 1;
+    for (int i = it - 1; i >= 0; --i) {
+        double acc = g[i];
+        for (int l = i + 1; l < it; ++l) acc -= R[size_t(l) * ld + i] * y[l];
+        const double d = R[size_t(i) * ld + i];
+        y[i] = d != 0.0 ? acc / d : 0.0;
+    }
+}
+
+// err[j] = sqrt(err[j]) for the iterates that exist, -1 after them
+__global__ void err_finish_kernel(double *err, const SolverState *st, int k)
+{
+    for (int j = 0; j <= k; ++j) err[j] = j <= st->iters ? sqrt(err[j]) : -1.0;
+}
+
 __global__ void backsolve_kernel(const double *R, const double *g, double *y, const SolverState *st, int k)
 {
     const int it = st->iters;
@@ -621,10 +663,8 @@ static cudaError_t apply_B(const GeomDev &g, int b_kind, float *sino, const doub
         if (e == cudaSuccess) e = launch_voxel_B(g, b.ypad, out_vol, stop, st);
         return e;
     }
-    // exact transpose A^T
-    e = cudaMemsetAsync(out_vol, 0, size_t(g.nx) * g.ny * g.nz * sizeof(float), st);
-    if (e == cudaSuccess) e = launch_joseph_At(g, sino, out_vol, stop, st);
-    return e;
+    // exact transpose A^T (the projector's copies serve as its accumulators)
+    return launch_joseph_At(g, sino, out_vol, b.Xc, b.Yc, stop, st);
 }
 
 static ct_status check_common(const ct_geom *geom, const float *b, int k, const float *x,
@@ -654,6 +694,8 @@ struct GmresWs {
     float *tvol = nullptr;  // AB-GMRES: B v_j
     double *H = nullptr, *H2 = nullptr, *R = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr,
            *resid = nullptr, *y = nullptr, *partials = nullptr;
+    double *err = nullptr;  // squared distances of the iterates to a reference image
+    int *cnt = nullptr;     // iterate count for the error history
     SolverState *st = nullptr;
     const void *vec(int i) const
     {
@@ -687,6 +729,8 @@ static bool carve_gmres(Arena &ar, const GeomDev &g, int k, bool ab, int b_kind,
     w.resid = ar.take<double>(ld);
     w.y = ar.take<double>(k);
     w.partials = ar.take<double>(partials_count());
+    w.err = ar.take<double>(ld);
+    w.cnt = ar.take<int>(1);
     w.st = ar.take<SolverState>(1);
     return w.st != nullptr;
 }
@@ -765,7 +809,8 @@ static ct_status open_ws(Arena &ar, size_t bytes, const ct_solve_opts &o, cudaSt
 // BA-GMRES
 // ---------------------------------------------------------------------------
 static ct_status bagmres(const ct_geom *geom, const float *b, int k, float *x, double *resid_hist,
-                         const ct_solve_opts &o, int *iters_done, cudaStream_t s)
+                         const ct_solve_opts &o, int *iters_done, cudaStream_t s, const float *x_ref = nullptr,
+                         double *err_hist = nullptr)
 {
     const GeomDev &g = geom->g;
     const size_t n = geom->n;
@@ -803,6 +848,34 @@ static ct_status bagmres(const ct_geom *geom, const float *b, int k, float *x, d
         }
         if (e == cudaSuccess) e = arnoldi_orthogonalise(w, w.q, j, k, n, o, s);
     }
+    // distance of every iterate x_j = V_j y_j to x_ref (x_out is the scratch
+    // image; the final x_k is formed after)
+    if (x_ref && e == cudaSuccess) {
+        const unsigned vb = red_blocks(n);
+        e = mgs_pass(1, const_cast<float *>(x_ref), nullptr, nullptr, nullptr, n, w.partials, &w.st->counter,
+                     nullptr, &w.err[0], nullptr, nullptr, s);
+        for (int j = 1; j <= k && e == cudaSuccess; ++j) {
+            {
+                ProfScope prof(PK_SMALL, s);
+                iterate_count_kernel<<<1, 1, 0, s>>>(w.st, j, w.cnt);
+                backsolve_count_kernel<<<1, 1, 0, s>>>(w.R, w.g, w.y, w.cnt, k);
+            }
+            e = w.vbf16 ? combine_t(static_cast<const __nv_bfloat16 *>(w.V), w.ldv, k, n, w.y, w.cnt, x, s)
+                        : combine(static_cast<const float *>(w.V), w.ldv, k, n, w.y, w.cnt, x, s);
+            if (e == cudaSuccess) {
+                ProfScope prof(PK_CGLS_VEC, s);
+                diff_sumsq_kernel<<<vb, RED_BLOCK, 0, s>>>(x, x_ref, n, w.partials, &w.st->counter, &w.err[j],
+                                                           nullptr);
+                e = cudaGetLastError();
+            }
+        }
+        if (e == cudaSuccess) {
+            { ProfScope prof(PK_SMALL, s); err_finish_kernel<<<1, 1, 0, s>>>(w.err, w.st, k); }
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess && err_hist)
+            e = cudaMemcpyAsync(err_hist, w.err, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, s);
+    }
     if (e == cudaSuccess) {
         { ProfScope prof(PK_SMALL, s); backsolve_kernel<<<1, 1, 0, s>>>(w.R, w.g, w.y, w.st, k); }
         e = cudaGetLastError();
@@ -816,6 +889,79 @@ static ct_status bagmres(const ct_geom *geom, const float *b, int k, float *x, d
     }
     rc = finish_solve(w.st, w.resid, k, resid_hist, iters_done, s, "ct_bagmres_solve");
     arena_close(ar);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Restarted BA-GMRES(m): cycles of m iterations, each on the residual
+// system B A dx = B (b - A x) from dx = 0, then x += dx.
+// ---------------------------------------------------------------------------
+__global__ void sub_kernel(float *__restrict__ out, const float *__restrict__ a, const float *__restrict__ b,
+                           size_t len)
+{
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < len; i += size_t(gridDim.x) * blockDim.x)
+        out[i] = a[i] - b[i];
+}
+
+__global__ void add_kernel(float *__restrict__ x, const float *__restrict__ d, size_t len)
+{
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < len; i += size_t(gridDim.x) * blockDim.x)
+        x[i] += d[i];
+}
+
+static ct_status bagmres_restarted(const ct_geom *geom, const float *b, int m, int cycles, float *x,
+                                   double *resid_hist, const ct_solve_opts &o, int *iters_done, cudaStream_t s)
+{
+    const GeomDev &g = geom->g;
+    const size_t n = geom->n, mm = geom->m;
+    const size_t copies = size_t(g.nzp) * g.nx * g.pitchX + size_t(g.nzp) * g.ny * g.pitchY;
+    float *buf = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&buf), sizeof(float) * (copies + 2 * mm + n), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(CT_ENOMEM, "ct_bagmres_restarted: %zu bytes of scratch: %s",
+                         sizeof(float) * (copies + 2 * mm + n), cudaGetErrorString(e));
+    }
+    float *Xc = buf, *Yc = buf + size_t(g.nzp) * g.nx * g.pitchX;
+    float *ax = buf + copies, *rb = ax + mm, *dx = rb + mm;
+    const unsigned blocks = unsigned(std::min<size_t>((std::max(n, mm) + 255) / 256, size_t(num_sms()) * 16));
+    std::vector<double> hist(size_t(m) + 1);
+    int total = 0;
+    ct_status rc = CT_OK;
+    e = cudaMemsetAsync(x, 0, n * sizeof(float), s);
+    if (resid_hist)
+        for (int i = 0; i <= m * cycles; ++i) resid_hist[i] = -1.0;
+    for (int c = 0; c < cycles && e == cudaSuccess; ++c) {
+        const float *rhs = b;
+        if (c > 0) {   // rb = b - A x
+            e = launch_plane_copies(g, x, nullptr, nullptr, Xc, Yc, nullptr, s);
+            if (e == cudaSuccess) e = launch_joseph_A(g, Xc, Yc, ax, plain_layout(g), nullptr, s);
+            if (e == cudaSuccess) {
+                sub_kernel<<<blocks, 256, 0, s>>>(rb, b, ax, mm);
+                e = cudaGetLastError();
+            }
+            rhs = rb;
+        }
+        if (e != cudaSuccess) break;
+        int it = 0;
+        rc = bagmres(geom, rhs, m, dx, hist.data(), o, &it, s);
+        if (rc != CT_OK && rc != CT_BREAKDOWN_LUCKY) break;
+        add_kernel<<<blocks, 256, 0, s>>>(x, dx, n);
+        e = cudaGetLastError();
+        if (resid_hist) {
+            if (c == 0) resid_hist[0] = hist[0];
+            for (int j = 1; j <= it; ++j) resid_hist[total + j] = hist[j];
+        }
+        total += it;
+        // a tolerance stop (relative to this cycle's start) or a breakdown ends the solve
+        if (it < m || rc == CT_BREAKDOWN_LUCKY) break;
+        if (o.tol > 0.0 && resid_hist && resid_hist[total] <= o.tol * resid_hist[0]) break;
+    }
+    cudaError_t e2 = cudaFreeAsync(buf, s);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (iters_done) *iters_done = total;
+    if (e != cudaSuccess) return cuda_error(e, "ct_bagmres_restarted");
     return rc;
 }
 
@@ -879,6 +1025,7 @@ static ct_status abgmres(const ct_geom *geom, const float *b, int k, float *x, d
 struct VjpWs {
     GmresWs gm;
     float *t = nullptr, *tf = nullptr;   // sinogram-space temporaries
+    float *Xa = nullptr, *Ya = nullptr;  // A^T accumulators (the projector's copy layout)
 };
 
 static void carve_vjp(Arena &ar, const GeomDev &g, int k, int b_kind, VjpWs &w)
@@ -889,6 +1036,8 @@ static void carve_vjp(Arena &ar, const GeomDev &g, int k, int b_kind, VjpWs &w)
     w.gm.V = ar.take<float>(w.gm.ldv * size_t(k + 1));
     w.t = ar.take<float>(m);
     w.tf = b_kind == CT_B_FBP ? ar.take<float>(m) : nullptr;
+    w.Xa = ar.take<float>(size_t(g.nzp) * g.nx * g.pitchX);
+    w.Ya = ar.take<float>(size_t(g.nzp) * g.ny * g.pitchY);
     const size_t ld = size_t(k) + 1;
     w.gm.H = ar.take<double>(ld * k);
     w.gm.H2 = ar.take<double>(ld);
@@ -968,8 +1117,7 @@ static ct_status bagmres_vjp(const ct_geom *geom, const float *gx, int k, float 
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = apply_Bt(g, o.b_kind, vj, w.t, w.tf, sino, stop, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(q, 0, n * sizeof(float), s);
-        if (e == cudaSuccess) e = launch_joseph_At(g, sino, q, stop, s);
+        if (e == cudaSuccess) e = launch_joseph_At(g, sino, q, w.Xa, w.Ya, stop, s);
         if (e == cudaSuccess) e = arnoldi_orthogonalise(gm, q, j, k, n, o, s);
     }
     if (e == cudaSuccess) {
@@ -1165,6 +1313,30 @@ ct_status ct_bagmres_solve_host(const ct_geom *geom, const float *b_host, int k,
     cudaFreeAsync(bd, s);
     if (e != cudaSuccess) return cuda_error(e, "ct_bagmres_solve_host copy");
     return rc;
+}
+
+ct_status ct_bagmres_solve_err(const ct_geom *geom, const float *b_dev, int k, float *x_out_dev,
+                               const float *x_ref_dev, double *resid_hist, double *err_hist,
+                               const ct_solve_opts *opts, int *iters_done, void *stream)
+{
+    ct_solve_opts o = resolve_opts(opts);
+    ct_status rc = check_common(geom, b_dev, k, x_out_dev, &o);
+    if (rc != CT_OK) return rc;
+    if (!x_ref_dev || !err_hist) return set_error(CT_EINVAL, "ct_bagmres_solve_err: NULL x_ref or err_hist");
+    return bagmres(geom, b_dev, k, x_out_dev, resid_hist, o, iters_done, static_cast<cudaStream_t>(stream),
+                   x_ref_dev, err_hist);
+}
+
+ct_status ct_bagmres_restarted(const ct_geom *geom, const float *b_dev, int m, int cycles, float *x_out_dev,
+                               double *resid_hist, const ct_solve_opts *opts, int *iters_done, void *stream)
+{
+    ct_solve_opts o = resolve_opts(opts);
+    ct_status rc = check_common(geom, b_dev, m, x_out_dev, &o);
+    if (rc != CT_OK) return rc;
+    if (cycles < 1 || size_t(m) * cycles > 1u << 20)
+        return set_error(CT_EINVAL, "ct_bagmres_restarted: cycles must be >= 1 and m * cycles <= 2^20");
+    return bagmres_restarted(geom, b_dev, m, cycles, x_out_dev, resid_hist, o, iters_done,
+                             static_cast<cudaStream_t>(stream));
 }
 
 ct_status ct_abgmres_solve(const ct_geom *geom, const float *b_dev, int k, float *x_out_dev,

@@ -354,56 +354,194 @@ cudaError_t launch_joseph_A(const GeomDev &g, const float *Xc, const float *Yc, 
 }
 
 // ---------------------------------------------------------------------------
-// x += A^T y: the same ray walk, scattering the four bilinear weights of
-// every sample with FP32 atomics (grid-bounded, no padding needed).
+// x = A^T y, the exact transpose of the projector above: the same column
+// walk (A_VR rays of one detector column per thread, warp-uniform plane
+// range, the same sample positions and bilinear weights), scattering
+// instead of gathering.  Contributions go with FP32 atomics into
+// plane-major accumulators laid out like the projector's copies
+// (Xa[zp][x][yp] for x-dominant rays, Ya[zp][y][xp]), so the lanes of a
+// warp (consecutive u) add to neighbouring words of one row.  Within a
+// thread the rays of a column add to a two-row window per plane, as the
+// projector reads one: contributions to the same row are summed in
+// registers and a row is flushed (two atomics: cells b0 and b0 + 1) when
+// the window moves past it.  Samples on the zero border are skipped (they
+// are zero entries of A).  A last pass adds the two accumulators into x.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void scatter_add(float *x, const GeomDev &g, int xdom, int p, int b,
-                                            int z, float val)
-{
-    const int Nb = xdom ? g.ny : g.nx;
-    if (b < 0 || b >= Nb || z < 0 || z >= g.nz || val == 0.0f) return;
-    const int ix = xdom ? p : b;
-    const int iy = xdom ? b : p;
-    atomicAdd(x + (size_t(z) * g.ny + iy) * g.nx + ix, val);
-}
-
+template <int VR, bool WINDOW, bool ZCLAMP>
 __global__ void __launch_bounds__(A_BLOCK) joseph_At_kernel(GeomDev g, const float *__restrict__ y,
-                                                            float *__restrict__ x,
+                                                            float *__restrict__ Xa, float *__restrict__ Ya,
                                                             const int *__restrict__ stop)
 {
     if (stop && *stop) return;
-    const int ray = blockIdx.x * A_BLOCK + threadIdx.x;
-    const int per_view = g.nu * g.nv;
-    if (ray >= per_view * g.n_views) return;
-    const float yr = y[ray];
-    if (yr == 0.0f) return;
-    const int s = ray / per_view;
-    const int rem = ray - s * per_view;
-    const int iv = rem / g.nu;
-    const int iu = rem - iv * g.nu;
-    const RaySetup r = ray_setup(g, s, iv, iu);
-    const float val = yr * r.weight;
-    for (int p = r.p0; p <= r.p1; ++p) {
-        const float pm = float(p) - r.ca;
-        const float fb = fmaf(pm, r.gb, r.fbc);
-        const float fz = fmaf(pm, r.gz, r.fzc);
-        const float b0f = floorf(fb), z0f = floorf(fz);
-        const float wb = fb - b0f, wz = fz - z0f;
-        const int b0 = int(b0f), z0 = int(z0f);
-        scatter_add(x, g, r.xdom, p, b0, z0, val * (1.0f - wb) * (1.0f - wz));
-        scatter_add(x, g, r.xdom, p, b0 + 1, z0, val * wb * (1.0f - wz));
-        scatter_add(x, g, r.xdom, p, b0, z0 + 1, val * (1.0f - wb) * wz);
-        scatter_add(x, g, r.xdom, p, b0 + 1, z0 + 1, val * wb * wz);
+    const int lane_u = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int iv0 = (blockIdx.y * (A_BLOCK / 32) + (threadIdx.x >> 5)) * VR;
+    const int s = blockIdx.z;
+    const bool live = lane_u < g.nu && iv0 < g.nv;
+    const int iu = min(lane_u, g.nu - 1);
+    const int ivl = min(iv0 + VR - 1, g.nv - 1);
+
+    const float4 *vp = reinterpret_cast<const float4 *>(g.viewA + s);
+    const float4 a = __ldg(vp), b = __ldg(vp + 1);   // (dx0, dxu, dy0, dyu), (dzv, crossu, sx, sy)
+    const float u = (float(iu) - g.cu) * g.du;
+    const float dx = fmaf(u, a.y, a.x);
+    const float dy = fmaf(u, a.w, a.z);
+    const float cross = u * b.y;
+    const bool xdom = fabsf(dx) >= fabsf(dy);
+    const float da = xdom ? dx : dy;
+    const float inv_da = 1.0f / da;
+    const int Na = xdom ? g.nx : g.ny;
+    const int Nb = xdom ? g.ny : g.nx;
+    const float ca = xdom ? g.cx : g.cy;
+    const float gb = (xdom ? dy : dx) * inv_da;
+    const float cterm = cross * inv_da * g.inv_vox;
+    const float fbc = xdom ? g.cy - cterm : g.cx + cterm;
+    const float Sv = (xdom ? b.z : b.w) * g.inv_vox;
+    const float gz_step = g.dv * b.x * inv_da;
+    const float gz0 = (float(iv0) - g.cv) * gz_step;
+
+    // each ray's value times its step weight (zero past nv and for idle lanes)
+    float val[VR];
+    bool any = false;
+    {
+        const float dxy2 = fmaf(dx, dx, dy * dy);
+#pragma unroll
+        for (int i = 0; i < VR; ++i) {
+            const int iv = iv0 + i;
+            val[i] = 0.0f;
+            if (live && iv < g.nv) {
+                const float v = (float(iv) - g.cv) * g.dv;
+                const float dz = v * b.x;
+                const float w = g.vox * sqrtf(fmaf(dz, dz, dxy2)) * fabsf(inv_da);
+                val[i] = y[(size_t(s) * g.nv + iv) * g.nu + iu] * w;
+                any = any || val[i] != 0.0f;
+            }
+        }
+    }
+
+    int p0 = 0, p1 = Na - 1;
+    clip_planes(fbc, gb, -1.0f, float(Nb), ca, Na, p0, p1);
+    {
+        const float gzl = (float(ivl) - g.cv) * gz_step;
+        int q0 = 0, q1 = Na - 1, r0 = 0, r1 = Na - 1;
+        clip_planes(fmaf(-Sv, gz0, g.cz), gz0, -1.0f, float(g.nz), ca, Na, q0, q1);
+        clip_planes(fmaf(-Sv, gzl, g.cz), gzl, -1.0f, float(g.nz), ca, Na, r0, r1);
+        p0 = max(p0, min(q0, r0));
+        p1 = min(p1, max(q1, r1));
+    }
+    if (!any) {   // nothing to add: this thread's rays do not widen the warp's range
+        p0 = Na;
+        p1 = -1;
+    }
+    p0 = __reduce_min_sync(0xffffffffu, p0);
+    p1 = __reduce_max_sync(0xffffffffu, p1);
+    p1 = min(p1, Na - 1);
+    if (!any) return;   // after the warp-wide reductions
+
+    float *__restrict__ base = xdom ? Xa : Ya;
+    const int pitch = xdom ? g.pitchX : g.pitchY;
+    const int zstride = Na * pitch;
+    const int bmax = Nb, zmax = g.nz;
+
+    for (int p = p0; p <= p1; ++p) {
+        const float pm = float(p) - ca;
+        const float fb = fmaf(pm, gb, fbc);
+        const float b0f = floorf(fb);
+        const float wb = fb - b0f;
+        const int b0 = min(max(int(b0f), -PAD_A), bmax);
+        const bool bl = b0 >= 0, bh = b0 + 1 < Nb;   // the two cells inside the grid
+        if (!bl && !bh) continue;
+        float *rowp = base + (PAD_A * Na + p) * pitch + b0 + PAD_A;   // (z = 0, plane p, b0)
+        const float q = pm - Sv;
+        const float fz0 = fmaf(gz0, q, g.cz);
+        const float dzr = gz_step * q;
+        // adds a row's summed contribution r to cells b0, b0 + 1 of grid row z
+        auto flush = [&](int z, float r) {
+            if (r == 0.0f || z < 0 || z >= zmax) return;
+            float *c = rowp + z * zstride;
+            if (bl) atomicAdd(c, r * (1.0f - wb));
+            if (bh) atomicAdd(c + 1, r * wb);
+        };
+        int zc = 0;
+        float acc_lo = 0.0f, acc_hi = 0.0f;   // rows zc and zc + 1
+#pragma unroll
+        for (int i = 0; i < VR; ++i) {
+            const float fz = fmaf(float(i), dzr, fz0);
+            const float z0f = floorf(fz);
+            const float wz = fz - z0f;
+            const int z0 = ZCLAMP ? min(max(int(z0f), -PAD_A), zmax) : int(z0f);
+            const float c_lo = val[i] * (1.0f - wz), c_hi = val[i] * wz;
+            if (!WINDOW) {
+                flush(z0, c_lo);
+                flush(z0 + 1, c_hi);
+            } else if (i == 0) {
+                zc = z0;
+                acc_lo = c_lo;
+                acc_hi = c_hi;
+            } else if (z0 == zc) {
+                acc_lo += c_lo;
+                acc_hi += c_hi;
+            } else {   // z0 == zc + 1: row zc is complete
+                flush(zc, acc_lo);
+                zc = z0;
+                acc_lo = acc_hi + c_lo;
+                acc_hi = c_hi;
+            }
+        }
+        if (WINDOW) {
+            flush(zc, acc_lo);
+            flush(zc + 1, acc_hi);
+        }
     }
 }
 
-cudaError_t launch_joseph_At(const GeomDev &g, const float *y, float *x, const int *stop,
+// x[z][y][x] = Xa[z][x][y] + Ya[z][y][x] over the grid (padded indices)
+__global__ void __launch_bounds__(256) unplane_kernel(GeomDev g, const float *__restrict__ Xa,
+                                                      const float *__restrict__ Ya, float *__restrict__ x,
+                                                      const int *__restrict__ stop)
+{
+    if (stop && *stop) return;
+    __shared__ float tile[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32, z = blockIdx.z;
+    const size_t zp = size_t(z) + PAD_A;
+    // tile[xl][yl] = Xa[zp][x0 + xl][y0 + yl + PAD_A], read along y
+    for (int r = ty; r < 32; r += 8) {
+        const int xx = x0 + r, yy = y0 + tx;
+        tile[r][tx] = (xx < g.nx && yy < g.ny) ? Xa[(zp * g.nx + xx) * g.pitchX + yy + PAD_A] : 0.0f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int yy = y0 + r, xx = x0 + tx;
+        if (xx < g.nx && yy < g.ny)
+            x[(size_t(z) * g.ny + yy) * g.nx + xx] = tile[tx][r] + Ya[(zp * g.ny + yy) * g.pitchY + xx + PAD_A];
+    }
+}
+
+cudaError_t launch_joseph_At(const GeomDev &g, const float *y, float *x, float *Xa, float *Ya, const int *stop,
                              cudaStream_t st)
 {
-    const long long m = (long long)g.nu * g.nv * g.n_views;
-    const unsigned blocks = unsigned((m + A_BLOCK - 1) / A_BLOCK);
     ProfScope prof(PK_JOSEPH_AT, st);
-    joseph_At_kernel<<<blocks, A_BLOCK, 0, st>>>(g, y, x, stop);
+    cudaError_t e = cudaMemsetAsync(Xa, 0, sizeof(float) * size_t(g.nzp) * g.nx * g.pitchX, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(Ya, 0, sizeof(float) * size_t(g.nzp) * g.ny * g.pitchY, st);
+    if (e != cudaSuccess) return e;
+    constexpr int WPB = A_BLOCK / 32;
+    if (g.nv == 1) {
+        dim3 grid((g.nu + 31) / 32, (g.nv + WPB - 1) / WPB, g.n_views);
+        joseph_At_kernel<1, false, true><<<grid, A_BLOCK, 0, st>>>(g, y, Xa, Ya, stop);
+    } else {
+        constexpr int VR = A_VR;
+        dim3 grid((g.nu + 31) / 32, (g.nv + WPB * VR - 1) / (WPB * VR), g.n_views);
+        if (g.a_window && g.a_zsafe)
+            joseph_At_kernel<VR, true, false><<<grid, A_BLOCK, 0, st>>>(g, y, Xa, Ya, stop);
+        else if (g.a_window)
+            joseph_At_kernel<VR, true, true><<<grid, A_BLOCK, 0, st>>>(g, y, Xa, Ya, stop);
+        else
+            joseph_At_kernel<VR, false, true><<<grid, A_BLOCK, 0, st>>>(g, y, Xa, Ya, stop);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 ublock(32, 8), ugrid((g.nx + 31) / 32, (g.ny + 31) / 32, g.nz);
+    unplane_kernel<<<ugrid, ublock, 0, st>>>(g, Xa, Ya, x, stop);
     return cudaGetLastError();
 }
 
@@ -432,8 +570,14 @@ extern "C" ct_status ct_adjoint_At(const ct_geom *geom, const float *y_dev, floa
 {
     if (!geom || !y_dev || !x_dev) return set_error(CT_EINVAL, "ct_adjoint_At: NULL argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CT_CUDA(cudaMemsetAsync(x_dev, 0, geom->n * sizeof(float), st));
-    cudaError_t e = launch_joseph_At(geom->g, y_dev, x_dev, nullptr, st);
+    const GeomDev &g = geom->g;
+    Arena ar;
+    ct_status rc = arena_open(ar, plane_copies_bytes(g), nullptr, 0, st);
+    if (rc != CT_OK) return rc;
+    float *Xa = ar.take<float>(size_t(g.nzp) * g.nx * g.pitchX);
+    float *Ya = ar.take<float>(size_t(g.nzp) * g.ny * g.pitchY);
+    cudaError_t e = launch_joseph_At(g, y_dev, x_dev, Xa, Ya, nullptr, st);
+    arena_close(ar);
     if (e != cudaSuccess) return cuda_error(e, "ct_adjoint_At launch");
     return CT_OK;
 }

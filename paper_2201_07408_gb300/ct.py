@@ -62,6 +62,8 @@ SIGNATURES = {
     "ct_ramp_F": (_i, [_vp, _vp, _vp, _i, _vp]),
     "ct_bagmres_solve": (_i, [_vp, _vp, _i, _vp, _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
     "ct_bagmres_solve_host": (_i, [_vp, _vp, _i, _vp, _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
+    "ct_bagmres_solve_err": (_i, [_vp, _vp, _i, _vp, _vp, _P(_d), _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
+    "ct_bagmres_restarted": (_i, [_vp, _vp, _i, _i, _vp, _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
     "ct_abgmres_solve": (_i, [_vp, _vp, _i, _vp, _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
     "ct_cgls_solve": (_i, [_vp, _vp, _i, _vp, _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
     "ct_bagmres_vjp": (_i, [_vp, _vp, _i, _vp, _P(_d), _P(ct_solve_opts), _P(_i), _vp]),
@@ -309,6 +311,53 @@ def ct_bagmres_solve_host(geom, b_host, k, x_out_host, opts=None, stream=None, w
                                      resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opts),
                                      ctypes.byref(iters), _stream(stream, d))
     _check("ct_bagmres_solve_host", st, allow=(CT_OK, CT_BREAKDOWN_LUCKY))
+    return SolveResult(status=st, iters=iters.value, resid=resid)
+
+
+def _torch_workspace(geom, k, solver, opts):
+    nbytes = ct_workspace_bytes(geom, k, solver, opts)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=geom.device)
+    opts.workspace = ctypes.c_void_p(ws.data_ptr())
+    opts.workspace_bytes = nbytes
+    return ws
+
+
+def ct_bagmres_solve_err(geom, b, k, x_out, x_ref, opts=None, stream=None, workspace="torch"):
+    """BA-GMRES with the image error of every iterate: returns
+    (SolveResult, err) with err[j] = ||x_j - x_ref|| (numpy, k+1; -1 after
+    the last iteration done)."""
+    d = geom.device
+    if opts is None:
+        opts = make_opts()
+    ws = _torch_workspace(geom, k, CT_SOLVER_BA, opts) if workspace == "torch" else None
+    resid = np.zeros(int(k) + 1, dtype=np.float64)
+    err = np.zeros(int(k) + 1, dtype=np.float64)
+    iters = ctypes.c_int(0)
+    st = lib().ct_bagmres_solve_err(geom.handle, _ptr(b, geom.m, "b", d), int(k), _ptr(x_out, geom.n, "x_out", d),
+                                    _ptr(x_ref, geom.n, "x_ref", d),
+                                    resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    err.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opts),
+                                    ctypes.byref(iters), _stream(stream, d))
+    del ws
+    _check("ct_bagmres_solve_err", st, allow=(CT_OK, CT_BREAKDOWN_LUCKY))
+    return SolveResult(status=st, iters=iters.value, resid=resid), err
+
+
+def ct_bagmres_restarted(geom, b, m, cycles, x_out, opts=None, stream=None, workspace="torch") -> SolveResult:
+    """Restarted BA-GMRES(m): `cycles` cycles of m iterations, each on the
+    residual system; resid has m*cycles + 1 entries."""
+    d = geom.device
+    if opts is None:
+        opts = make_opts()
+    ws = _torch_workspace(geom, m, CT_SOLVER_BA, opts) if workspace == "torch" else None
+    resid = np.zeros(int(m) * int(cycles) + 1, dtype=np.float64)
+    iters = ctypes.c_int(0)
+    st = lib().ct_bagmres_restarted(geom.handle, _ptr(b, geom.m, "b", d), int(m), int(cycles),
+                                    _ptr(x_out, geom.n, "x_out", d),
+                                    resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opts),
+                                    ctypes.byref(iters), _stream(stream, d))
+    del ws
+    _check("ct_bagmres_restarted", st, allow=(CT_OK, CT_BREAKDOWN_LUCKY))
     return SolveResult(status=st, iters=iters.value, resid=resid)
 
 

@@ -291,3 +291,71 @@ def test_full_size_256_bagmres_properties(ct, b_kind, k):
     c = float((s1 * Bb).sum() / (s1 * s1).sum())
     r1 = float(torch.linalg.vector_norm(Bb - c * s1))
     assert abs(r1 - r[1]) <= 1e-4 * r[0], (r1, r[1])
+
+
+def test_error_history_matches_oracle(ct):
+    """ct_bagmres_solve_err: err[j] = ||x_j - x_true|| of every iterate (the
+    semi-convergence curve, Sec. III Fig. 4) against the FP64 oracle's
+    iterates, each within max(1e-4 ||x_j||, 3 d_j), d_j the distance between
+    the oracle's iterate and its own run with FP32-class (1e-6) operator
+    error; x_out is the plain solve's x_k."""
+    spec, k = ci.CONE_SMALL, 12
+    b, x_true = data_for(spec)
+    g = ct.Geometry.from_spec(spec)
+    x = torch.empty(spec.vol_shape, device="cuda")
+    res, err = ct.ct_bagmres_solve_err(g, dev(b), k, x, dev(x_true), ct.make_opts(b_kind="fbp"))
+    x_plain = torch.empty_like(x)
+    res_plain = ct.ct_bagmres_solve(g, dev(b), k, x_plain, ct.make_opts(b_kind="fbp"))
+    assert torch.equal(x, x_plain) and np.array_equal(res.resid, res_plain.resid)
+    ops = oracle.Operators(spec, "fbp")
+    b64 = b.astype(np.float64).reshape(-1)
+    ref = krylov.ba_gmres(ops.A, ops.B, b64, k, keep_basis=False)
+    rng = np.random.default_rng(97)
+    pert = krylov.ba_gmres(_perturbed(ops.A, rng), _perturbed(ops.B, rng), b64, k, keep_basis=False)
+    xt = x_true.reshape(-1)
+    assert abs(err[0] - np.linalg.norm(xt)) <= 1e-5 * np.linalg.norm(xt)
+    for j in range(1, k + 1):
+        xj = ref["x"][j - 1]
+        tol = max(SOLVE_TOL * np.linalg.norm(xj), 3 * np.linalg.norm(pert["x"][j - 1] - xj))
+        assert abs(err[j] - np.linalg.norm(xj - xt)) <= tol, (j, err[j], np.linalg.norm(xj - xt), tol)
+
+
+def test_error_history_marks_iterations_not_done(ct):
+    spec = ci.CONE_ANISO
+    b, x_true = data_for(spec, noise=0.0)
+    g = ct.Geometry.from_spec(spec)
+    x = torch.empty(spec.vol_shape, device="cuda")
+    res, err = ct.ct_bagmres_solve_err(g, dev(b), 30, x, dev(x_true), ct.make_opts(b_kind="fbp", tol=1e-2))
+    assert 0 < res.iters < 30
+    assert np.all(err[res.iters + 1:] == -1.0) and np.all(err[:res.iters + 1] >= 0.0)
+
+
+@pytest.mark.parametrize("spec,b_kind", [(ci.CONE_SMALL, "un"), (ci.PAR2D_64, "fbp")],
+                         ids=lambda v: getattr(v, "name", str(v)))
+def test_restarted_matches_oracle(ct, spec, b_kind):
+    """ct_bagmres_restarted, 3 cycles of GMRES(5), against the FP64 oracle's
+    restarted solve (same tolerance rule as the unrestarted solves)."""
+    m, cycles = 5, 3
+    b, _ = data_for(spec)
+    g = ct.Geometry.from_spec(spec)
+    x = torch.empty(spec.vol_shape, device="cuda")
+    res = ct.ct_bagmres_restarted(g, dev(b), m, cycles, x, ct.make_opts(b_kind=b_kind))
+    ref, tol_x, tol_r = oracle_with_sensitivity(
+        lambda A, B, bb, k: krylov.ba_gmres_restarted(A, B, bb, m, cycles), spec, b_kind, b, m * cycles)
+    assert res.iters == m * cycles
+    assert np.max(np.abs(res.resid - ref["resid"])) <= tol_r * ref["resid"][0]
+    assert rel(host(x), ref["x_final"]) <= tol_x, (rel(host(x), ref["x_final"]), tol_x)
+    assert np.all(np.diff(res.resid) <= 1e-6 * res.resid[0])
+
+
+def test_restarted_single_cycle_equals_solve(ct):
+    spec = ci.CONE_ANISO
+    b, _ = data_for(spec)
+    g = ct.Geometry.from_spec(spec)
+    x1 = torch.empty(spec.vol_shape, device="cuda")
+    x2 = torch.empty(spec.vol_shape, device="cuda")
+    r1 = ct.ct_bagmres_solve(g, dev(b), 7, x1, ct.make_opts(b_kind="un"))
+    r2 = ct.ct_bagmres_restarted(g, dev(b), 7, 1, x2, ct.make_opts(b_kind="un"))
+    assert torch.equal(x1, x2) and np.array_equal(r1.resid, r2.resid)
+    with pytest.raises(ct.CTError):
+        ct.ct_bagmres_restarted(g, dev(b), 7, 0, x2)

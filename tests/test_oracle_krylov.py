@@ -173,3 +173,33 @@ def test_unmatched_cgls_diverges_while_ba_gmres_converges():
     ba = krylov.ba_gmres(lambda v: A @ v, lambda v: B @ v, b, 50)
     assert np.all(np.diff(ba["resid"]) <= 1e-12 * ba["resid"][0])
     assert ba["resid"][-1] < 1e-3 * ba["resid"][0]
+
+
+def test_restarted_ba_gmres_is_a_sequence_of_krylov_least_squares(tiny2d):
+    """GMRES(m), Sec. II: each cycle's correction is the least-squares
+    minimiser of ||B r_c - B A dx|| over K_m(BA, B r_c), r_c = b - A x_c,
+    built here from an explicit Krylov matrix; the history is the
+    concatenation of the cycles' residuals, non-increasing, and its cycle
+    ends equal the recomputed ||B (b - A x)||."""
+    A, B, b = tiny2d
+    m, cycles = 4, 3
+    out = krylov.ba_gmres_restarted(lambda v: A @ v, lambda v: B @ v, b, m, cycles)
+    S = B @ A
+    x = np.zeros(A.shape[1])
+    for c in range(cycles):
+        rc = B @ (b - A @ x)
+        Q, _ = np.linalg.qr(krylov_matrix(S, rc, m))
+        z, *_ = np.linalg.lstsq(S @ Q, rc, rcond=None)
+        x = x + Q @ z
+        assert abs(out["resid"][(c + 1) * m] - np.linalg.norm(B @ (b - A @ x))) <= 1e-10 * out["resid"][0]
+    np.testing.assert_allclose(out["x_final"], x, rtol=1e-7, atol=1e-7 * np.abs(x).max())
+    assert out["resid"].size == m * cycles + 1
+    assert np.all(np.diff(out["resid"]) <= 1e-12 * out["resid"][0])
+
+
+def test_restarted_single_cycle_is_plain_ba_gmres(tiny2d):
+    A, B, b = tiny2d
+    plain = krylov.ba_gmres(lambda v: A @ v, lambda v: B @ v, b, 6)
+    rest = krylov.ba_gmres_restarted(lambda v: A @ v, lambda v: B @ v, b, 6, 1)
+    np.testing.assert_allclose(rest["x_final"], plain["x_final"], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(rest["resid"], plain["resid"], rtol=1e-12)
