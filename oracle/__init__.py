@@ -69,6 +69,11 @@ def lib():
             "or_ramp_F": [g, P(d), P(d)],
             "or_ramp_Ft": [g, P(d), P(d)],
             "or_ramp_F_rows": [g, P(d), P(L), L, P(d)],
+            "or_project_S": [g, P(d), P(d)],
+            "or_project_S_rays": [g, P(d), P(L), L, P(d)],
+            "or_adjoint_St": [g, P(d), P(d)],
+            "or_s_row": [g, L, P(L), P(d)],
+            "or_s_row_capacity": [g],
             "or_a_row": [g, L, P(L), P(d)],
             "or_b_row": [g, L, P(L), P(d)],
             "or_a_row_capacity": [g],
@@ -80,8 +85,8 @@ def lib():
             f = getattr(_lib, name)
             f.argtypes = args
             f.restype = None
-        for name in ("or_a_row", "or_b_row", "or_a_row_capacity", "or_b_row_capacity",
-                     "or_num_threads"):
+        for name in ("or_a_row", "or_b_row", "or_s_row", "or_a_row_capacity", "or_b_row_capacity",
+                     "or_s_row_capacity", "or_num_threads"):
             getattr(_lib, name).restype = ctypes.c_int
         _lib.or_ramp_scale.restype = ctypes.c_double
     return _lib
@@ -127,6 +132,40 @@ def project_A_rays(g, x, rays):
     out = np.empty(rays.size)
     lib().or_project_A_rays(ctypes.byref(_geom(g)), _dptr(x), _lptr(rays), rays.size, _dptr(out))
     return out
+
+
+def project_S(g, x):
+    """y = A_S x (line-intersection projector: ray length inside each voxel)."""
+    x = _f64(x, g.n)
+    y = np.empty(g.m)
+    lib().or_project_S(ctypes.byref(_geom(g)), _dptr(x), _dptr(y))
+    return y.reshape(g.sino_shape)
+
+
+def project_S_rays(g, x, rays):
+    """(A_S x)[rays] for flat ray indices."""
+    x = _f64(x, g.n)
+    rays = np.ascontiguousarray(rays, dtype=np.int64)
+    out = np.empty(rays.size)
+    lib().or_project_S_rays(ctypes.byref(_geom(g)), _dptr(x), _lptr(rays), rays.size, _dptr(out))
+    return out
+
+
+def adjoint_St(g, y):
+    """x = A_S^T y (exact transpose of A_S)."""
+    y = _f64(y, g.m)
+    x = np.empty(g.n)
+    lib().or_adjoint_St(ctypes.byref(_geom(g)), _dptr(y), _dptr(x))
+    return x.reshape(g.vol_shape)
+
+
+def s_row(g, ray):
+    """(voxel indices, lengths) of row `ray` of A_S."""
+    cap = lib().or_s_row_capacity(ctypes.byref(_geom(g)))
+    idx = np.empty(cap, dtype=np.int64)
+    w = np.empty(cap)
+    cnt = lib().or_s_row(ctypes.byref(_geom(g)), int(ray), _lptr(idx), _dptr(w))
+    return idx[:cnt].copy(), w[:cnt].copy()
 
 
 def adjoint_At(g, y):
@@ -217,18 +256,20 @@ def b_row(g, voxel):
 
 
 class Operators:
-    """The pair (A, B) of one geometry as flat-vector callables for the solvers."""
+    """The pair (A, B) of one geometry as flat-vector callables for the solvers;
+    projector "joseph" (A) or "siddon" (A_S)."""
 
-    def __init__(self, g, b_kind="un"):
+    def __init__(self, g, b_kind="un", projector="joseph"):
         self.g = g
         self.b_kind = b_kind
+        self.siddon = projector == "siddon"
 
     def A(self, x):
-        return project_A(self.g, x).reshape(-1)
+        return (project_S if self.siddon else project_A)(self.g, x).reshape(-1)
 
     def B(self, y):
         if self.b_kind in ("At", "at"):
-            return adjoint_At(self.g, y).reshape(-1)
+            return (adjoint_St if self.siddon else adjoint_At)(self.g, y).reshape(-1)
         return backproject_B(self.g, y, filtered=self.b_kind == "fbp").reshape(-1)
 
 

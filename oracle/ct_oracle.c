@@ -18,6 +18,8 @@
  *   F      m x m   ramp filter per detector row (cosine weight, Ram-Lak,
  *                  linear convolution), so that B_FBP = B_un F.
  *   A^T, B_un^T, F^T  exact transposes.
+ *   A_S    m x n   the line-intersection projector itself (the length of
+ *                  the ray inside each voxel), and its transpose.
  *
  * A and A^T are both built from one enumerator of the nonzeros of a row of A
  * (a_row), and B_un and B_un^T from one enumerator of a row of B_un (b_row),
@@ -193,6 +195,150 @@ int or_b_row(const or_geom *g, long voxel, long *idx, double *w)
         }
     }
     return cnt;
+}
+
+/*
+ * Nonzeros of row `ray` of the line-intersection projector A_S (Sec. III:
+ * the paper's matrix elements are the lengths of the ray inside each
+ * voxel).  Voxel (i,j,k) is the box of side vox around its centre; the grid
+ * is the box [-N vox/2, N vox/2] along each axis (2D: the ray lies in z = 0,
+ * inside the single slice).  The ray point is S + alpha d.  The values of
+ * alpha where the ray crosses a voxel boundary plane, together with its
+ * entry and exit of the grid box, are sorted; each interval between
+ * consecutive values lies in one voxel (the one containing the interval's
+ * midpoint), and its length is the interval times |d|.  Zero-length
+ * intervals (simultaneous crossings) are skipped.
+ */
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+int or_s_row_capacity(const or_geom *g) { return g->nx + g->ny + g->nz + 4; }
+
+int or_s_row(const or_geom *g, long ray, long *idx, double *w)
+{
+    double S[3], d[3];
+    ray_of(g, ray, S, d);
+    const int N[3] = {g->nx, g->ny, g->nz};
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        hi[a] = 0.5 * N[a] * g->vox;
+        lo[a] = -hi[a];
+    }
+    /* entry and exit of the grid box */
+    double a_in = -INFINITY, a_out = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) {
+            if (!(S[a] > lo[a] && S[a] < hi[a])) return 0;
+            continue;
+        }
+        double t1 = (lo[a] - S[a]) / d[a], t2 = (hi[a] - S[a]) / d[a];
+        if (t1 > t2) { double t = t1; t1 = t2; t2 = t; }
+        if (t1 > a_in) a_in = t1;
+        if (t2 < a_out) a_out = t2;
+    }
+    if (!(a_out > a_in)) return 0;
+    int cap = g->nx + g->ny + g->nz + 3;
+    double *al = malloc(sizeof(double) * (size_t)(cap + 2));
+    int na = 0;
+    al[na++] = a_in;
+    al[na++] = a_out;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) continue;
+        for (int k = 0; k <= N[a]; ++k) {
+            double t = (lo[a] + k * g->vox - S[a]) / d[a];
+            if (t > a_in && t < a_out) al[na++] = t;
+        }
+    }
+    qsort(al, (size_t)na, sizeof(double), cmp_double);
+    double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    int cnt = 0;
+    for (int m = 0; m + 1 < na; ++m) {
+        double len = (al[m + 1] - al[m]) * dn;
+        if (len <= 0.0) continue;
+        double am = 0.5 * (al[m] + al[m + 1]);
+        long id[3];
+        for (int a = 0; a < 3; ++a) {
+            double f = (S[a] + am * d[a] - lo[a]) / g->vox;
+            long i = (long)floor(f);
+            if (i < 0) i = 0;
+            if (i >= N[a]) i = N[a] - 1;
+            id[a] = i;
+        }
+        idx[cnt] = (id[2] * g->ny + id[1]) * (long)g->nx + id[0];
+        w[cnt] = len;
+        ++cnt;
+    }
+    free(al);
+    return cnt;
+}
+
+/* y = A_S x, and x = A_S^T y, with the line-intersection projector. */
+void or_project_S(const or_geom *g, const double *x, double *y)
+{
+    long m = (long)g->n_views * g->nv * g->nu;
+    int cap = or_s_row_capacity(g);
+#pragma omp parallel
+    {
+        long *idx = malloc(sizeof(long) * cap);
+        double *w = malloc(sizeof(double) * cap);
+#pragma omp for schedule(dynamic, 256)
+        for (long r = 0; r < m; ++r) {
+            int cnt = or_s_row(g, r, idx, w);
+            double acc = 0.0;
+            for (int e = 0; e < cnt; ++e)
+                acc += w[e] * x[idx[e]];
+            y[r] = acc;
+        }
+        free(idx);
+        free(w);
+    }
+}
+
+void or_project_S_rays(const or_geom *g, const double *x, const long *rays, long count, double *out)
+{
+    int cap = or_s_row_capacity(g);
+#pragma omp parallel
+    {
+        long *idx = malloc(sizeof(long) * cap);
+        double *w = malloc(sizeof(double) * cap);
+#pragma omp for schedule(dynamic, 16)
+        for (long e = 0; e < count; ++e) {
+            int cnt = or_s_row(g, rays[e], idx, w);
+            double acc = 0.0;
+            for (int q = 0; q < cnt; ++q)
+                acc += w[q] * x[idx[q]];
+            out[e] = acc;
+        }
+        free(idx);
+        free(w);
+    }
+}
+
+void or_adjoint_St(const or_geom *g, const double *y, double *x)
+{
+    long n = (long)g->nx * g->ny * g->nz;
+    long m = (long)g->n_views * g->nv * g->nu;
+    int cap = or_s_row_capacity(g);
+    memset(x, 0, sizeof(double) * n);
+#pragma omp parallel
+    {
+        long *idx = malloc(sizeof(long) * cap);
+        double *w = malloc(sizeof(double) * cap);
+#pragma omp for schedule(dynamic, 256)
+        for (long r = 0; r < m; ++r) {
+            int cnt = or_s_row(g, r, idx, w);
+            for (int e = 0; e < cnt; ++e) {
+                double val = w[e] * y[r];
+#pragma omp atomic
+                x[idx[e]] += val;
+            }
+        }
+        free(idx);
+        free(w);
+    }
 }
 
 /* y = A x  (x: n, y: m). */
