@@ -65,6 +65,12 @@ typedef enum { CT_PARALLEL_2D = 0, CT_CONE_3D = 1 } ct_geom_kind;
 
 typedef enum { CT_F32 = 0, CT_BF16 = 1 } ct_dtype;
 
+/* Which discretisation the projector A uses (Sec. III). */
+typedef enum {
+    CT_PROJ_JOSEPH = 0,  /* Joseph: one bilinear sample per voxel-centre plane (default) */
+    CT_PROJ_SIDDON = 1   /* line intersection: the length of the ray inside each voxel */
+} ct_projector;
+
 /* Which back-projector B a call uses (Sec. III). */
 typedef enum {
     CT_B_UN = 0,   /* B_un: voxel-driven back-projection, bilinear detector interpolation */
@@ -89,6 +95,7 @@ typedef struct {
     int sino_dtype;            /* storage of the back-projector's working sinogram: CT_F32 or
                                   CT_BF16.  Arithmetic is FP32 (FP64 for the least squares) and
                                   caller buffers are FP32 whatever the storage. */
+    int projector;             /* ct_projector: the A (and A^T) of every call on this geometry */
 } ct_geom_desc;
 
 typedef struct ct_geom ct_geom;
@@ -124,10 +131,14 @@ CT_API size_t ct_geom_n(const ct_geom *geom);
 CT_API size_t ct_geom_m(const ct_geom *geom);
 
 /* y = A x: ray-driven projector (Sec. I Eq. 1; Sec. III "ray-driven
- * cone-beam projector").  Read as Joseph's method: for each ray, one
- * bilinear sample on every voxel-centre plane of the ray's dominant axis
- * (x when |d_x| >= |d_y|), neighbours outside the grid count as zero, sum
- * times the step vox*|d|/|d_a|.  x: n floats, y: m floats (overwritten). */
+ * cone-beam projector").  CT_PROJ_JOSEPH: for each ray, one bilinear
+ * sample on every voxel-centre plane of the ray's dominant axis (x when
+ * |d_x| >= |d_y|), neighbours outside the grid count as zero, sum times the
+ * step vox*|d|/|d_a|.  CT_PROJ_SIDDON: the sum over the voxels the ray
+ * crosses of the voxel value times the length of the ray inside the voxel
+ * (voxel (i,j,k) is the cube of edge vox around its centre), the
+ * line-intersection method the paper names.  x: n floats, y: m floats
+ * (overwritten). */
 CT_API ct_status ct_project_A(const ct_geom *geom, const float *x_dev, float *y_dev, void *stream);
 
 /* x = B y: back-projection (Sec. III).  b_kind CT_B_UN: voxel-driven

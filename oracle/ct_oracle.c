@@ -207,7 +207,12 @@ int or_b_row(const or_geom *g, long voxel, long *idx, double *w)
  * entry and exit of the grid box, are sorted; each interval between
  * consecutive values lies in one voxel (the one containing the interval's
  * midpoint), and its length is the interval times |d|.  Zero-length
- * intervals (simultaneous crossings) are skipped.
+ * intervals (simultaneous crossings) are skipped.  A direction component
+ * below 1e-12 |d| counts as zero: such a ray runs parallel to those
+ * boundary planes, and one lying in a plane belongs to the voxels on its
+ * positive side (a measure-zero case that the method leaves open; the
+ * rounded cosine of a 90-degree view would otherwise split the ray between
+ * the two sides at an arbitrary point).
  */
 static int cmp_double(const void *a, const void *b)
 {
@@ -222,6 +227,9 @@ int or_s_row(const or_geom *g, long ray, long *idx, double *w)
     double S[3], d[3];
     ray_of(g, ray, S, d);
     const int N[3] = {g->nx, g->ny, g->nz};
+    double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int a = 0; a < 3; ++a)
+        if (fabs(d[a]) <= 1e-12 * dn) d[a] = 0.0;
     double lo[3], hi[3];
     for (int a = 0; a < 3; ++a) {
         hi[a] = 0.5 * N[a] * g->vox;
@@ -253,7 +261,6 @@ int or_s_row(const or_geom *g, long ray, long *idx, double *w)
         }
     }
     qsort(al, (size_t)na, sizeof(double), cmp_double);
-    double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     int cnt = 0;
     for (int m = 0; m + 1 < na; ++m) {
         double len = (al[m + 1] - al[m]) * dn;

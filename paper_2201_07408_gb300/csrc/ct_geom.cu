@@ -122,6 +122,8 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         return set_error(CT_EINVAL, "voxel and pixel sizes must be positive");
     if (!std::isfinite(d->angle_start_rad) || !std::isfinite(d->angle_span_rad))
         return set_error(CT_EINVAL, "view angles must be finite");
+    if (d->projector != CT_PROJ_JOSEPH && d->projector != CT_PROJ_SIDDON)
+        return set_error(CT_EINVAL, "projector must be CT_PROJ_JOSEPH or CT_PROJ_SIDDON");
     if ((d->vol_dtype != CT_F32 && d->vol_dtype != CT_BF16) || (d->sino_dtype != CT_F32 && d->sino_dtype != CT_BF16))
         return set_error(CT_EINVAL, "storage dtypes must be CT_F32 or CT_BF16");
     if (d->kind == CT_PARALLEL_2D && (d->nz != 1 || d->nv != 1))
@@ -182,6 +184,7 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     k.pitchY = d->nx + 2 * PAD_A;
     k.padv = padv;
     k.vol_bf16 = d->vol_dtype == CT_BF16;
+    k.siddon = d->projector == CT_PROJ_SIDDON;
     k.sino_bf16 = d->sino_dtype == CT_BF16;
     k.nvp = d->nv + 2 * k.padv;
     k.pitchU = d->nu + 2 * PAD_U;

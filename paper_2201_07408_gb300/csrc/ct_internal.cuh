@@ -90,6 +90,8 @@ struct GeomDev {
     int fft_n;
     const float2 *fft_tw;
     const float *fft_h;
+    // projector: 0 Joseph, 1 line intersection (Siddon)
+    int siddon;
 };
 
 // Layout of a sinogram buffer that an operator writes.
@@ -223,13 +225,18 @@ __device__ __forceinline__ void store_sino_pair(float *out, const SinoLayout &la
 // (the Arnoldi normalisation), as float or, when g.vol_bf16, as bf16.
 cudaError_t launch_plane_copies(const GeomDev &g, const float *vol, const double *scale, void *basis_out,
                                 float *Xc, float *Yc, const int *stop, cudaStream_t st);
-// y = A x from the plane copies, written in `lay`.
-cudaError_t launch_joseph_A(const GeomDev &g, const float *Xc, const float *Yc, float *y,
+// y = A x from the plane copies (Joseph; the line-intersection projector
+// reads Yc only), written in `lay`.
+cudaError_t launch_project_A(const GeomDev &g, const float *Xc, const float *Yc, float *y,
                             SinoLayout lay, const int *stop, cudaStream_t st);
 // x = A^T y (overwritten); y in plain layout.  Xa, Ya: accumulators of the
 // projector's copy sizes (contents overwritten).
-cudaError_t launch_joseph_At(const GeomDev &g, const float *y, float *x, float *Xa, float *Ya, const int *stop,
+cudaError_t launch_project_At(const GeomDev &g, const float *y, float *x, float *Xa, float *Ya, const int *stop,
                              cudaStream_t st);
+// the line-intersection projector and its transpose (ct_siddon.cu); x overwritten
+cudaError_t launch_siddon_A(const GeomDev &g, const float *Yc, float *y, SinoLayout lay, const int *stop,
+                            cudaStream_t st);
+cudaError_t launch_siddon_At(const GeomDev &g, const float *y, float *x, const int *stop, cudaStream_t st);
 
 // --- back-projector (ct_backproject.cu) ------------------------------------------
 // Copies a plain sinogram into the padded layout, scaled by (*scale) when

@@ -664,7 +664,7 @@ static cudaError_t apply_B(const GeomDev &g, int b_kind, float *sino, const doub
         return e;
     }
     // exact transpose A^T (the projector's copies serve as its accumulators)
-    return launch_joseph_At(g, sino, out_vol, b.Xc, b.Yc, stop, st);
+    return launch_project_At(g, sino, out_vol, b.Xc, b.Yc, stop, st);
 }
 
 static ct_status check_common(const ct_geom *geom, const float *b, int k, const float *x,
@@ -840,10 +840,10 @@ static ct_status bagmres(const ct_geom *geom, const float *b, int k, float *x, d
         if (e != cudaSuccess) break;
         // q = B A v_j
         if (o.b_kind == CT_B_UN) {
-            e = launch_joseph_A(g, w.ob.Xc, w.ob.Yc, w.ob.ypad, padded_layout(g), stop, s);
+            e = launch_project_A(g, w.ob.Xc, w.ob.Yc, w.ob.ypad, padded_layout(g), stop, s);
             if (e == cudaSuccess) e = launch_voxel_B(g, w.ob.ypad, w.q, stop, s);
         } else {
-            e = launch_joseph_A(g, w.ob.Xc, w.ob.Yc, w.ob.t, plain_layout(g), stop, s);
+            e = launch_project_A(g, w.ob.Xc, w.ob.Yc, w.ob.t, plain_layout(g), stop, s);
             if (e == cudaSuccess) e = apply_B(g, o.b_kind, w.ob.t, nullptr, false, w.ob, w.q, stop, s, nullptr);
         }
         if (e == cudaSuccess) e = arnoldi_orthogonalise(w, w.q, j, k, n, o, s);
@@ -935,7 +935,7 @@ static ct_status bagmres_restarted(const ct_geom *geom, const float *b, int m, i
         const float *rhs = b;
         if (c > 0) {   // rb = b - A x
             e = launch_plane_copies(g, x, nullptr, nullptr, Xc, Yc, nullptr, s);
-            if (e == cudaSuccess) e = launch_joseph_A(g, Xc, Yc, ax, plain_layout(g), nullptr, s);
+            if (e == cudaSuccess) e = launch_project_A(g, Xc, Yc, ax, plain_layout(g), nullptr, s);
             if (e == cudaSuccess) {
                 sub_kernel<<<blocks, 256, 0, s>>>(rb, b, ax, mm);
                 e = cudaGetLastError();
@@ -995,7 +995,7 @@ static ct_status abgmres(const ct_geom *geom, const float *b, int k, float *x, d
         float *q = Vf + size_t(j + 1) * w.ldv;
         e = apply_B(g, o.b_kind, vj, &w.st->inv_norm, true, w.ob, w.tvol, stop, s, nullptr);
         if (e == cudaSuccess) e = launch_plane_copies(g, w.tvol, nullptr, nullptr, w.ob.Xc, w.ob.Yc, stop, s);
-        if (e == cudaSuccess) e = launch_joseph_A(g, w.ob.Xc, w.ob.Yc, q, plain_layout(g), stop, s);
+        if (e == cudaSuccess) e = launch_project_A(g, w.ob.Xc, w.ob.Yc, q, plain_layout(g), stop, s);
         if (e == cudaSuccess) e = arnoldi_orthogonalise(w, q, j, k, m, o, s);
     }
     if (e == cudaSuccess) {
@@ -1117,7 +1117,7 @@ static ct_status bagmres_vjp(const ct_geom *geom, const float *gx, int k, float 
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = apply_Bt(g, o.b_kind, vj, w.t, w.tf, sino, stop, s);
-        if (e == cudaSuccess) e = launch_joseph_At(g, sino, q, w.Xa, w.Ya, stop, s);
+        if (e == cudaSuccess) e = launch_project_At(g, sino, q, w.Xa, w.Ya, stop, s);
         if (e == cudaSuccess) e = arnoldi_orthogonalise(gm, q, j, k, n, o, s);
     }
     if (e == cudaSuccess) {
@@ -1203,7 +1203,7 @@ static ct_status cgls(const ct_geom *geom, const float *b, int k, float *x, doub
     for (int j = 1; j <= k && e == cudaSuccess; ++j) {
         // q = A p ; delta = ||q||^2
         e = launch_plane_copies(g, w.p, nullptr, nullptr, w.ob.Xc, w.ob.Yc, stop, s);
-        if (e == cudaSuccess) e = launch_joseph_A(g, w.ob.Xc, w.ob.Yc, w.q, plain_layout(g), stop, s);
+        if (e == cudaSuccess) e = launch_project_A(g, w.ob.Xc, w.ob.Yc, w.q, plain_layout(g), stop, s);
         if (e == cudaSuccess)
             e = mgs_pass(1, w.q, nullptr, nullptr, nullptr, m, w.partials, ctr, nullptr, &st->delta, stop, nullptr, s);
         if (e == cudaSuccess) {
@@ -1221,7 +1221,7 @@ static ct_status cgls(const ct_geom *geom, const float *b, int k, float *x, doub
         }
         if (e == cudaSuccess && data) {
             e = launch_plane_copies(g, x, nullptr, nullptr, w.ob.Xc, w.ob.Yc, stop, s);
-            if (e == cudaSuccess) e = launch_joseph_A(g, w.ob.Xc, w.ob.Yc, w.ax, plain_layout(g), stop, s);
+            if (e == cudaSuccess) e = launch_project_A(g, w.ob.Xc, w.ob.Yc, w.ax, plain_layout(g), stop, s);
             if (e == cudaSuccess) {
                 { ProfScope prof(PK_CGLS_VEC, s); diff_sumsq_kernel<<<vb, RED_BLOCK, 0, s>>>(b, w.ax, m, w.partials, ctr, &st->data_rr, stop); }
                 e = cudaGetLastError();

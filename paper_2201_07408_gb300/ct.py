@@ -22,6 +22,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libct.so")
 CT_OK, CT_EINVAL, CT_ENOMEM, CT_ECUDA, CT_ENONFINITE, CT_ETIMEOUT, CT_BREAKDOWN_LUCKY = range(7)
 CT_PARALLEL_2D, CT_CONE_3D = 0, 1
 CT_F32, CT_BF16 = 0, 1
+CT_PROJ_JOSEPH, CT_PROJ_SIDDON = 0, 1
+PROJECTORS = {"joseph": CT_PROJ_JOSEPH, "siddon": CT_PROJ_SIDDON}
 CT_B_UN, CT_B_FBP, CT_B_AT = 0, 1, 2
 CT_SOLVER_BA, CT_SOLVER_AB, CT_SOLVER_CGLS, CT_SOLVER_BA_VJP = 0, 1, 2, 3
 
@@ -37,7 +39,7 @@ class ct_geom_desc(ctypes.Structure):
                 ("angle_start_rad", ctypes.c_double), ("angle_span_rad", ctypes.c_double),
                 ("nu", ctypes.c_int), ("nv", ctypes.c_int), ("du_mm", ctypes.c_double),
                 ("dv_mm", ctypes.c_double), ("sod_mm", ctypes.c_double), ("sdd_mm", ctypes.c_double),
-                ("vol_dtype", ctypes.c_int), ("sino_dtype", ctypes.c_int)]
+                ("vol_dtype", ctypes.c_int), ("sino_dtype", ctypes.c_int), ("projector", ctypes.c_int)]
 
 
 class ct_solve_opts(ctypes.Structure):
@@ -149,15 +151,16 @@ class Geometry:
 
     Fields follow ct_geom_desc; ``from_spec`` accepts any object with the
     attributes kind, nx, ny, nz, vox, n_views, ang0, span, nu, nv, du, dv,
-    sod, sdd."""
+    sod, sdd.  ``projector``: "joseph" (default) or "siddon"."""
 
     def __init__(self, kind, nx, ny, nz, vox, n_views, ang0, span, nu, nv, du, dv, sod=0.0, sdd=0.0,
-                 device=None, vol_dtype=CT_F32, sino_dtype=CT_F32):
+                 device=None, vol_dtype=CT_F32, sino_dtype=CT_F32, projector="joseph"):
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
                                    else torch.device(device).index or 0)
         self.desc = ct_geom_desc(int(kind), int(nx), int(ny), int(nz), float(vox), int(n_views), float(ang0),
                                  float(span), int(nu), int(nv), float(du), float(dv), float(sod), float(sdd),
-                                 _dtype(vol_dtype), _dtype(sino_dtype))
+                                 _dtype(vol_dtype), _dtype(sino_dtype),
+                                 PROJECTORS[projector] if isinstance(projector, str) else int(projector))
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check("ct_geom_create", lib().ct_geom_create(ctypes.byref(self.desc), ctypes.byref(self._h)))
@@ -167,10 +170,10 @@ class Geometry:
         self.sino_shape = (int(n_views), int(nv), int(nu))
 
     @classmethod
-    def from_spec(cls, spec, device=None, vol_dtype=CT_F32, sino_dtype=CT_F32):
+    def from_spec(cls, spec, device=None, vol_dtype=CT_F32, sino_dtype=CT_F32, projector="joseph"):
         return cls(spec.kind, spec.nx, spec.ny, spec.nz, spec.vox, spec.n_views, spec.ang0, spec.span,
                    spec.nu, spec.nv, spec.du, spec.dv, spec.sod, spec.sdd, device=device,
-                   vol_dtype=vol_dtype, sino_dtype=sino_dtype)
+                   vol_dtype=vol_dtype, sino_dtype=sino_dtype, projector=projector)
 
     @property
     def handle(self):

@@ -207,3 +207,66 @@ def test_operator_errors_are_reported(ct):
     y = torch.zeros(spec.m, device="cuda")
     with pytest.raises(ct.CTError):
         ct.ct_ramp_F(g, y, y)
+
+
+# --- line-intersection projector (CT_PROJ_SIDDON) -------------------------------
+SIDDON_CASES = [ci.CONE_SMALL, ci.CONE_ANISO, ci.CONE_THIN, ci.PAR2D_ANISO, ci.PAR2D_64]
+
+
+@pytest.mark.parametrize("spec", SIDDON_CASES, ids=lambda s: s.name)
+@pytest.mark.parametrize("kind", ["phantom", "random"])
+def test_siddon_A_matches_oracle(ct, spec, kind):
+    g = ct.Geometry.from_spec(spec, projector="siddon")
+    x = volume_input(spec, kind)
+    y = host(ct.project_A(g, dev(x)))
+    ref = oracle.project_S(spec, x.astype(np.float64))
+    assert rel(y, ref) <= OP_TOL, rel(y, ref)
+
+
+# Line-intersection lengths are ill-conditioned where a ray runs nearly
+# parallel to a grid plane: a position error e moves the crossing of that
+# plane by e/|h_a| along the ray (h the unit direction).  FP32 ray
+# coordinates carry e ~ 1e-6 voxel, so single voxel lengths differ from the
+# FP64 oracle's by up to ~1e-4 voxel (a float32 emulation of the walk shows
+# 1e-5 voxel typical, 3e-4 at most, on cone_small).  A_S sums them along
+# the ray, where the shifts cancel in pairs (1e-6 relative); A_S^T adds each
+# into its own voxel, where they do not, and random data measures 1.1e-5.
+SIDDON_T_TOL = 3e-5
+
+
+@pytest.mark.parametrize("spec", SIDDON_CASES, ids=lambda s: s.name)
+def test_siddon_At_matches_oracle(ct, spec):
+    g = ct.Geometry.from_spec(spec, projector="siddon")
+    y = ci.random_vector(spec.m, seed=74).astype(np.float32).reshape(spec.sino_shape)
+    x = host(ct.adjoint_At(g, dev(y)))
+    ref = oracle.adjoint_St(spec, y.astype(np.float64))
+    assert rel(x, ref) <= SIDDON_T_TOL, rel(x, ref)
+
+
+def test_siddon_bf16_volume_and_full_size_rays(ct):
+    """BF16 storage reads the same walk from the rounded copy; at 256^3 the
+    walk is checked on sampled rays against the oracle."""
+    spec = ci.CONE_SMALL
+    g = ct.Geometry.from_spec(spec, projector="siddon", vol_dtype="bf16")
+    x = volume_input(spec, "phantom")
+    y = host(ct.project_A(g, dev(x)))
+    xr = torch.from_numpy(x).to(torch.bfloat16).float().numpy()
+    assert rel(y, oracle.project_S(spec, xr.astype(np.float64))) <= OP_TOL
+    spec = ci.CONE_256
+    g = ct.Geometry.from_spec(spec, projector="siddon")
+    x = ci.phantom(spec)[0]
+    y = host(ct.project_A(g, dev(x))).reshape(-1)
+    rays = ci.sample_indices(spec.m, 2000, seed=75)
+    ref = oracle.project_S_rays(spec, x.astype(np.float64), rays)
+    assert rel(y[rays], ref) <= OP_TOL, rel(y[rays], ref)
+
+
+def test_siddon_gpu_dot_product(ct):
+    spec = ci.CONE_ANISO
+    g = ct.Geometry.from_spec(spec, projector="siddon")
+    x = dev(ci.random_vector(spec.n, seed=76).reshape(spec.vol_shape))
+    y = dev(ci.random_vector(spec.m, seed=77).reshape(spec.sino_shape))
+    ax = ct.project_A(g, x).double()
+    lhs = float((ax * y.double()).sum())
+    rhs = float((x.double() * ct.adjoint_At(g, y).double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * float(ax.norm() * y.double().norm())

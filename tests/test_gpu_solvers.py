@@ -359,3 +359,22 @@ def test_restarted_single_cycle_equals_solve(ct):
     assert torch.equal(x1, x2) and np.array_equal(r1.resid, r2.resid)
     with pytest.raises(ct.CTError):
         ct.ct_bagmres_restarted(g, dev(b), 7, 0, x2)
+
+
+@pytest.mark.parametrize("spec,b_kind,k", [(ci.CONE_SMALL, "un", 12), (ci.PAR2D_64, "fbp", 15)],
+                         ids=lambda v: getattr(v, "name", str(v)))
+def test_bagmres_with_siddon_projector_matches_oracle(ct, spec, b_kind, k):
+    """BA-GMRES with the line-intersection A and the same unmatched B."""
+    b, _ = data_for(spec)
+    g = ct.Geometry.from_spec(spec, projector="siddon")
+    x = torch.empty(spec.vol_shape, device="cuda")
+    res = ct.ct_bagmres_solve(g, dev(b), k, x, ct.make_opts(b_kind=b_kind))
+    ops = oracle.Operators(spec, b_kind, projector="siddon")
+    b64 = b.astype(np.float64).reshape(-1)
+    ref = krylov.ba_gmres(ops.A, ops.B, b64, k, keep_basis=False)
+    rng = np.random.default_rng(97)
+    pert = krylov.ba_gmres(_perturbed(ops.A, rng), _perturbed(ops.B, rng), b64, k, keep_basis=False)
+    tol_x = max(SOLVE_TOL, 3 * rel(pert["x_final"], ref["x_final"]))
+    tol_r = max(SOLVE_TOL, 3 * np.max(np.abs(pert["resid"] - ref["resid"])) / ref["resid"][0])
+    assert np.max(np.abs(res.resid - ref["resid"])) <= tol_r * ref["resid"][0]
+    assert rel(host(x), ref["x_final"]) <= tol_x, (rel(host(x), ref["x_final"]), tol_x)
