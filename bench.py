@@ -206,15 +206,18 @@ def aggregate_over_ranks(elapsed_s, iters, world, device=None):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the kernel on the workload, with the SHA-256 of the
-# kernel's source file at capture time: a changed source gives null (the
-# counters no longer describe the kernel).  The captures are summarised in
+# kernel's source file and the shared device header at capture time: a
+# changed source gives null (the counters may no longer describe the kernel).  The captures are summarised in
 # profiles/.
 NCU_TRAFFIC = {
-    # (kernel, storage, workload): (bytes per launch, source file, sha256)
-    ("voxel_B", "f32", "cone_256"): (1419528000 + 68819200, "ct_backproject.cu",
-                                     "f08091f1be1a0aa167c7e09df30fa5f549652930869b212a2aeb2a57b99af0e2"),
-    ("joseph_A", "f32", "cone_256"): (392276736 + 132639232, "ct_project.cu",
-                                      "85067cb99faad36d4df1152fa8907ba277baffa78decfda90f5ad1f71fe91131"),
+    # (kernel, storage, workload): (bytes per launch, source file,
+    # sha256 of that file followed by ct_internal.cuh at capture time)
+    ("voxel_B", "f32", "cone_256"): (1415970560 + 68444672, "ct_backproject.cu",
+                                     "eb55300ae338b650fe939231e067489d998d264a067d1a05ef292821fde63500"),
+    ("voxel_B", "bf16", "cone_256"): (565138944 + 61659392, "ct_backproject.cu",
+                                      "eb55300ae338b650fe939231e067489d998d264a067d1a05ef292821fde63500"),
+    ("joseph_A", "f32", "cone_256"): (399137024 + 133204736, "ct_project.cu",
+                                      "021c1ab5de5f00e4a7748ef3e700b1fea11618a412f07e43d50d782452eb9fb2"),
 }
 
 
@@ -224,14 +227,16 @@ def ncu_traffic(kernel, storage, workload):
     if not ent:
         return None
     nbytes, src, sha = ent
-    path = os.path.join(ROOT, "paper_2201_07408_gb300", "csrc", src)
+    csrc = os.path.join(ROOT, "paper_2201_07408_gb300", "csrc")
+    h = hashlib.sha256()
     try:
-        with open(path, "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != sha:
-                return None
+        # the kernel's file and the shared device header it inlines
+        for name in (src, "ct_internal.cuh"):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
     except OSError:
         return None
-    return nbytes
+    return nbytes if h.hexdigest() == sha else None
 
 
 def measured_peaks():

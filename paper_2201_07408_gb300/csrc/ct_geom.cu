@@ -214,12 +214,12 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     //   a_window: 0 <= sigma <= 0.98, so a two-row window per column suffices;
     //   a_zsafe:  |z| stays within the grid plus one voxel, so no clamp is needed;
     //             checked over the rows the threads compute, which run up to
-    //             the next multiple of A_VR past nv.
+    //             the next multiple of the rays per thread past nv.
     k.a_window = 0;
     k.a_zsafe = 1;
     if (cone) {
         double smin = 1e300, smax = -1e300;
-        const int nv_run = (d->nv + A_VR - 1) / A_VR * A_VR;
+        const int nv_run = (d->nv + A_VR_MAX - 1) / A_VR_MAX * A_VR_MAX;
         const double vmax = std::max(0.5 * (d->nv - 1), nv_run - 1 - 0.5 * (d->nv - 1)) * d->dv_mm;
         for (int s = 0; s < d->n_views; ++s) {
             double th = d->angle_start_rad + double(s) * d->angle_span_rad / double(d->n_views);

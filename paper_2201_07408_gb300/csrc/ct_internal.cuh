@@ -18,11 +18,19 @@ constexpr int PAD_A = 2;   // voxels, around the in-plane and z axes of the plan
 constexpr int PAD_U = 1;   // pixels, both ends of each detector row
 constexpr int PAD_V = 2;   // rows, above and below each view
 // rays per projector thread along a detector column (the last group of a
-// column runs past nv when nv is not a multiple; those rays are discarded)
+// column runs past nv when nv is not a multiple; those rays are discarded):
+// A_VR for A, AT_VR for its exact transpose (tuning; at 256^3, 16 rays took
+// A 5.31 / 5.74 ms with FP32 / bf16 copies and A^T 5.74 ms, against 5.39 /
+// 6.16 ms and 6.06 ms with 8 rays, and A 8.16 / 9.01 ms with 12)
 #ifndef CT_A_VR
-#define CT_A_VR 8
+#define CT_A_VR 16
+#endif
+#ifndef CT_AT_VR
+#define CT_AT_VR 16
 #endif
 constexpr int A_VR = CT_A_VR;
+constexpr int AT_VR = CT_AT_VR;
+constexpr int A_VR_MAX = A_VR > AT_VR ? A_VR : AT_VR;
 // consecutive z slices per back-projector thread (3D); the last run of a
 // column may pass nz: those slices are computed and discarded, and the
 // padded sinogram's row margin covers them too
@@ -67,6 +75,10 @@ struct GeomDev {
     //   Q[view][vp][up] = (S[v][u], S[v][u+1], S[v+1][u], S[v+1][u+1]) as float4,
     //   v = vp - padv, u = up - PAD_U, vp in [0, nv + 2 padv), up in [0, nu + 2 PAD_U),
     //   S zero outside the detector: the four bilinear neighbours of a sample in one load.
+    //   FP32 entries written a row pair at a time (the pad and ramp kernels) hold row
+    //   differences instead, (S[v][u], S[v][u+1] - S[v][u], S[v+1][u], S[v+1][u+1] - S[v+1][u]),
+    //   which interpolate in fewer operations (QuadForm); entries written value by value
+    //   (a projector's store_sino) and bf16 entries hold the four values.
     // padv (>= PAD_V) rows of zeros cover every voxel's projection, so the
     // back-projector's row index needs no clamp.
     int nvp, pitchU, padv;
@@ -115,8 +127,13 @@ __device__ __forceinline__ void store_sino(float *out, const SinoLayout &lay, in
 {
     const size_t e = (size_t(s) * lay.rows_per_view + iv + lay.row_off) * lay.pitch + iu + lay.col_off;
     if (lay.quads) {
-        // (v, u) is .x of entry (v, u), .y of (v, u-1), .z of (v-1, u), .w of (v-1, u-1)
+        // (v, u) is .x of entry (v, u), .y of (v, u-1), .z of (v-1, u), .w of (v-1, u-1).
+        // In the last column the entry's right neighbours (.y, .w) are S[.][nu] = 0:
+        // they are written here too, because a buffer that last held the
+        // row-difference form has -S[v][nu-1] there.  Every other slot off the
+        // detector is zero in both forms.
         const size_t up = e - lay.pitch;
+        const bool last_col = iu + 1 == lay.pitch - 2 * lay.col_off;
         if (lay.bf16) {
             __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(out);
             const __nv_bfloat16 h = __float2bfloat16_rn(val);
@@ -124,11 +141,19 @@ __device__ __forceinline__ void store_sino(float *out, const SinoLayout &lay, in
             o[4 * (e - 1) + 1] = h;
             o[4 * up + 2] = h;
             o[4 * (up - 1) + 3] = h;
+            if (last_col) {
+                o[4 * e + 1] = __float2bfloat16_rn(0.0f);
+                o[4 * up + 3] = __float2bfloat16_rn(0.0f);
+            }
         } else {
             out[4 * e] = val;
             out[4 * (e - 1) + 1] = val;
             out[4 * up + 2] = val;
             out[4 * (up - 1) + 3] = val;
+            if (last_col) {
+                out[4 * e + 1] = 0.0f;
+                out[4 * up + 3] = 0.0f;
+            }
         }
     } else {
         out[e] = val;
@@ -200,7 +225,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 // Stores the horizontal pair (S[v][u], S[v][u+1]) of a quad-layout
 // sinogram: it is the first half of entry (v, u) and the second half of
 // entry (v-1, u), one 8-byte (4-byte for bf16) store each.  u may be -1
-// (S[v][-1] = 0): the padded layout has that column.
+// (S[v][-1] = 0): the padded layout has that column.  FP32 halves are
+// stored in the row-difference form (S[v][u], S[v][u+1] - S[v][u]).
 __device__ __forceinline__ void store_sino_pair(float *out, const SinoLayout &lay, int s, int iv, int iu, float lo,
                                                 float hi)
 {
@@ -213,8 +239,8 @@ __device__ __forceinline__ void store_sino_pair(float *out, const SinoLayout &la
         o[2 * up + 1] = w;
     } else {
         float2 *o = reinterpret_cast<float2 *>(out);
-        o[2 * e] = make_float2(lo, hi);
-        o[2 * up + 1] = make_float2(lo, hi);
+        o[2 * e] = make_float2(lo, hi - lo);
+        o[2 * up + 1] = make_float2(lo, hi - lo);
     }
 }
 
@@ -247,9 +273,13 @@ cudaError_t launch_pad_sino(const GeomDev &g, float *src, const double *scale,
 // dst = F src (or F^T src) from a plain sinogram into layout `lay`.
 cudaError_t launch_ramp(const GeomDev &g, const float *src, float *dst, SinoLayout lay,
                         bool transpose, const int *stop, cudaStream_t st);
-// x = B_un y from the padded sinogram.
+// Form of the FP32 entries of a padded quad sinogram (bf16 entries always
+// hold the four values).
+enum QuadForm { QUAD_ROWDIFF, QUAD_CORNERS };
+// x = B_un y from the padded sinogram: QUAD_ROWDIFF after launch_pad_sino or
+// launch_ramp, QUAD_CORNERS after a projector wrote it with store_sino.
 cudaError_t launch_voxel_B(const GeomDev &g, const float *ypad, float *x, const int *stop,
-                           cudaStream_t st);
+                           cudaStream_t st, QuadForm form);
 // y += B_un^T x (y plain, zeroed by the caller).
 cudaError_t launch_voxel_Bt(const GeomDev &g, const float *x, float *y, const int *stop,
                             cudaStream_t st);

@@ -650,7 +650,7 @@ static cudaError_t apply_B(const GeomDev &g, int b_kind, float *sino, const doub
     cudaError_t e = cudaSuccess;
     if (b_kind == CT_B_UN) {
         e = launch_pad_sino(g, sino, scale, normalize, b.ypad, stop, st);
-        if (e == cudaSuccess) e = launch_voxel_B(g, b.ypad, out_vol, stop, st);
+        if (e == cudaSuccess) e = launch_voxel_B(g, b.ypad, out_vol, stop, st, QUAD_ROWDIFF);
         return e;
     }
     if (scale) {
@@ -660,7 +660,7 @@ static cudaError_t apply_B(const GeomDev &g, int b_kind, float *sino, const doub
     }
     if (b_kind == CT_B_FBP) {
         e = launch_ramp(g, sino, b.ypad, padded_layout(g), false, stop, st);
-        if (e == cudaSuccess) e = launch_voxel_B(g, b.ypad, out_vol, stop, st);
+        if (e == cudaSuccess) e = launch_voxel_B(g, b.ypad, out_vol, stop, st, QUAD_ROWDIFF);
         return e;
     }
     // exact transpose A^T (the projector's copies serve as its accumulators)
@@ -841,7 +841,7 @@ static ct_status bagmres(const ct_geom *geom, const float *b, int k, float *x, d
         // q = B A v_j
         if (o.b_kind == CT_B_UN) {
             e = launch_project_A(g, w.ob.Xc, w.ob.Yc, w.ob.ypad, padded_layout(g), stop, s);
-            if (e == cudaSuccess) e = launch_voxel_B(g, w.ob.ypad, w.q, stop, s);
+            if (e == cudaSuccess) e = launch_voxel_B(g, w.ob.ypad, w.q, stop, s, QUAD_CORNERS);
         } else {
             e = launch_project_A(g, w.ob.Xc, w.ob.Yc, w.ob.t, plain_layout(g), stop, s);
             if (e == cudaSuccess) e = apply_B(g, o.b_kind, w.ob.t, nullptr, false, w.ob, w.q, stop, s, nullptr);

@@ -199,13 +199,17 @@ __device__ __forceinline__ float row_lerp(const float *p, float wb)
 }
 
 // plane-loop unroll (tuning): 2 for FP32 copies, 4 for bf16 pairs (measured
-// at 256^3: 5.38 and 5.92 ms; unrolling the FP32 loop by 4 or the bf16 loop
-// by 2 took 5.78 and 7.58 ms); the rays per thread, A_VR, are in the shared
-// header
+// at 256^3 with 16 rays per thread: 5.31 and 5.74 ms; unrolling the FP32
+// loop by 1 or 4 took 8.44 and 5.63 ms, the bf16 loop by 2 8.76 ms); the
+// rays per thread, A_VR, are in the shared header
 #ifndef CT_A_PUNROLL
 #define CT_A_PUNROLL 2
 #endif
+#ifndef CT_A_PUNROLL_BF
+#define CT_A_PUNROLL_BF 4
+#endif
 constexpr int kAPlaneUnroll = CT_A_PUNROLL;
+constexpr int kAPlaneUnrollBF = CT_A_PUNROLL_BF;
 
 template <int VR, bool WINDOW, bool ZCLAMP, bool BF>
 __global__ void __launch_bounds__(A_BLOCK) joseph_A_kernel(GeomDev g, const float *__restrict__ Xc,
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(A_BLOCK) joseph_A_kernel(GeomDev g, const floa
 #pragma unroll
     for (int i = 0; i < VR; ++i) acc[i] = 0.0f;
 
-#pragma unroll (BF ? 4 : kAPlaneUnroll)
+#pragma unroll (BF ? kAPlaneUnrollBF : kAPlaneUnroll)
     for (int p = p0; p <= p1; ++p) {
         const float pm = float(p) - ca;
         const float fb = fmaf(pm, gb, fbc);
@@ -359,7 +363,7 @@ cudaError_t launch_project_A(const GeomDev &g, const float *Xc, const float *Yc,
 
 // ---------------------------------------------------------------------------
 // x = A^T y, the exact transpose of the projector above: the same column
-// walk (A_VR rays of one detector column per thread, warp-uniform plane
+// walk (AT_VR rays of one detector column per thread, warp-uniform plane
 // range, the same sample positions and bilinear weights), scattering
 // instead of gathering.  Contributions go with FP32 atomics into
 // plane-major accumulators laid out like the projector's copies
@@ -534,7 +538,7 @@ cudaError_t launch_project_At(const GeomDev &g, const float *y, float *x, float 
         dim3 grid((g.nu + 31) / 32, (g.nv + WPB - 1) / WPB, g.n_views);
         joseph_At_kernel<1, false, true><<<grid, A_BLOCK, 0, st>>>(g, y, Xa, Ya, stop);
     } else {
-        constexpr int VR = A_VR;
+        constexpr int VR = AT_VR;
         dim3 grid((g.nu + 31) / 32, (g.nv + WPB * VR - 1) / (WPB * VR), g.n_views);
         if (g.a_window && g.a_zsafe)
             joseph_At_kernel<VR, true, false><<<grid, A_BLOCK, 0, st>>>(g, y, Xa, Ya, stop);

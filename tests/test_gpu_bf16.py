@@ -81,6 +81,19 @@ def test_backproject_B_bf16_sinogram(ct, spec, b_kind):
         assert rel(x, ref) <= 1e-4
 
 
+def test_backproject_B_bf16_full_size_sampled(ct):
+    """B_un from a bf16 sinogram on the full 256^3 scan (16-slice runs per
+    thread, 360 views), on seeded voxels against the oracle applied to the
+    identically rounded sinogram."""
+    spec = ci.CONE_256
+    g = ct.Geometry.from_spec(spec, sino_dtype="bf16")
+    y = ci.random_vector(spec.m, 76, dtype=np.float32, positive=True).reshape(spec.sino_shape)
+    xb = ct.backproject_B(g, torch.from_numpy(y).cuda()).cpu().numpy().reshape(-1)
+    vox = ci.sample_indices(spec.n, 2000, seed=77)
+    ref = oracle.backproject_B_voxels(spec, round_bf16(y).astype(np.float64), vox)
+    assert rel(xb[vox], ref) <= 1e-5, rel(xb[vox], ref)
+
+
 @pytest.mark.parametrize("b_kind", ["un", "fbp"])
 def test_bagmres_bf16_storage(ct, b_kind):
     spec = ci.CONE_512_CUT64
