@@ -216,8 +216,8 @@ NCU_TRAFFIC = {
                                      "eb55300ae338b650fe939231e067489d998d264a067d1a05ef292821fde63500"),
     ("voxel_B", "bf16", "cone_256"): (565138944 + 61659392, "ct_backproject.cu",
                                       "eb55300ae338b650fe939231e067489d998d264a067d1a05ef292821fde63500"),
-    ("joseph_A", "f32", "cone_256"): (399137024 + 133204736, "ct_project.cu",
-                                      "021c1ab5de5f00e4a7748ef3e700b1fea11618a412f07e43d50d782452eb9fb2"),
+    ("joseph_A", "f32", "cone_256"): (410601984 + 137186816, "ct_project.cu",
+                                      "23a53af9d909bb77422f495dfb27483f672b92b055af07d7a0a5a41e0b616a6e"),
 }
 
 

@@ -210,9 +210,16 @@ __device__ __forceinline__ float row_lerp(const float *p, float wb)
 #endif
 constexpr int kAPlaneUnroll = CT_A_PUNROLL;
 constexpr int kAPlaneUnrollBF = CT_A_PUNROLL_BF;
+// resident blocks per SM that ptxas sizes the registers for (tuning): 5 for
+// FP32 copies (96 registers), 4 for bf16 pairs (128).  At 256^3 these took
+// 5.03 and 5.41 ms, against 5.29 and 5.73 ms with ptxas's own choice of 64
+// registers (8 blocks); 6 or 7 blocks gave 5.07 / 5.04 ms (FP32), 9 blocks
+// (56 registers) 8.5 ms.
+constexpr int kAMinBlocks = 5;
+constexpr int kAMinBlocksBF = 4;
 
 template <int VR, bool WINDOW, bool ZCLAMP, bool BF>
-__global__ void __launch_bounds__(A_BLOCK) joseph_A_kernel(GeomDev g, const float *__restrict__ Xc,
+__global__ void __launch_bounds__(A_BLOCK, BF ? kAMinBlocksBF : kAMinBlocks) joseph_A_kernel(GeomDev g, const float *__restrict__ Xc,
                                                            const float *__restrict__ Yc,
                                                            float *__restrict__ y, SinoLayout lay,
                                                            const int *__restrict__ stop)
