@@ -218,6 +218,8 @@ NCU_TRAFFIC = {
                                       "eb55300ae338b650fe939231e067489d998d264a067d1a05ef292821fde63500"),
     ("joseph_A", "f32", "cone_256"): (410601984 + 137186816, "ct_project.cu",
                                       "23a53af9d909bb77422f495dfb27483f672b92b055af07d7a0a5a41e0b616a6e"),
+    ("joseph_A", "bf16", "cone_256"): (429411840 + 153559040, "ct_project.cu",
+                                       "23a53af9d909bb77422f495dfb27483f672b92b055af07d7a0a5a41e0b616a6e"),
 }
 
 
