@@ -108,25 +108,18 @@ __device__ __forceinline__ void walk(const GeomDev &g, const RayWalk &w, F visit
     for (int n = 0; n < max_steps; ++n) {
         const float dt = fminf(dx, fminf(dy, dz));
         visit(ix, iy, iz, fmaxf(dt, 0.0f) * g.vox);
-        if (dx == dt) {
-            ix += sx;
-            if (ix < 0 || ix >= g.nx) break;
-            dx = tdx;
-            dy -= dt;
-            dz -= dt;
-        } else if (dy == dt) {
-            iy += sy;
-            if (iy < 0 || iy >= g.ny) break;
-            dy = tdy;
-            dx -= dt;
-            dz -= dt;
-        } else {
-            iz += sz;
-            if (iz < 0 || iz >= g.nz) break;
-            dz = tdz;
-            dx -= dt;
-            dy -= dt;
-        }
+        // the axis crossed first steps (ties go to x, then y); the others move
+        // dt closer to their next crossing.  Selects instead of branches: the
+        // lanes of a warp cross different axes, and a three-way branch would
+        // run all three paths one after the other.
+        const bool mx = dx == dt, my = !mx && dy == dt, mz = !mx && !my;
+        ix += mx ? sx : 0;
+        iy += my ? sy : 0;
+        iz += mz ? sz : 0;
+        dx = mx ? tdx : dx - dt;
+        dy = my ? tdy : dy - dt;
+        dz = mz ? tdz : dz - dt;
+        if (unsigned(ix) >= unsigned(g.nx) || unsigned(iy) >= unsigned(g.ny) || unsigned(iz) >= unsigned(g.nz)) break;
     }
 }
 
