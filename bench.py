@@ -217,9 +217,9 @@ NCU_TRAFFIC = {
     ("voxel_B", "bf16", "cone_256"): (565138944 + 61659392, "ct_backproject.cu",
                                       "eb55300ae338b650fe939231e067489d998d264a067d1a05ef292821fde63500"),
     ("joseph_A", "f32", "cone_256"): (410601984 + 137186816, "ct_project.cu",
-                                      "23a53af9d909bb77422f495dfb27483f672b92b055af07d7a0a5a41e0b616a6e"),
+                                      "e5c36ae4139e92ca3bfb2cb308078c2cb0ad1adacb65c5a41e47c0f5fe3c6304"),
     ("joseph_A", "bf16", "cone_256"): (429411840 + 153559040, "ct_project.cu",
-                                       "23a53af9d909bb77422f495dfb27483f672b92b055af07d7a0a5a41e0b616a6e"),
+                                       "e5c36ae4139e92ca3bfb2cb308078c2cb0ad1adacb65c5a41e47c0f5fe3c6304"),
 }
 
 

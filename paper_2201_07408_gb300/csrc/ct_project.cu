@@ -199,7 +199,7 @@ __device__ __forceinline__ float row_lerp(const float *p, float wb)
 }
 
 // plane-loop unroll (tuning): 2 for FP32 copies, 4 for bf16 pairs (measured
-// at 256^3 with 16 rays per thread: 5.31 and 5.74 ms; unrolling the FP32
+// at 256^3 with 16 rays per thread and 64 registers: 5.31 and 5.74 ms; unrolling the FP32
 // loop by 1 or 4 took 8.44 and 5.63 ms, the bf16 loop by 2 8.76 ms); the
 // rays per thread, A_VR, are in the shared header
 #ifndef CT_A_PUNROLL

@@ -86,10 +86,13 @@ __device__ __forceinline__ bool ray_walk(const GeomDev &g, int s, int iv, int iu
     return true;
 }
 
-// Calls visit(ix, iy, iz, length) for every voxel the ray crosses (the
-// per-axis state lives in scalars, so nothing is indexed at run time).
+// Calls visit(offset, length) for every voxel the ray crosses: offset =
+// base + ix + iy ystride + iz zstride, kept up to date step by step (32-bit:
+// ct_geom_create bounds every buffer below 2^31 elements), and the length
+// inside the voxel in voxel units.  The per-axis state lives in scalars, so
+// nothing is indexed at run time.
 template <typename F>
-__device__ __forceinline__ void walk(const GeomDev &g, const RayWalk &w, F visit)
+__device__ __forceinline__ void walk(const GeomDev &g, const RayWalk &w, int base, int ystride, int zstride, F visit)
 {
     // the voxel of the entry point: on the entry face the index is clamped
     // into the grid (the point lies on the boundary)
@@ -97,6 +100,8 @@ __device__ __forceinline__ void walk(const GeomDev &g, const RayWalk &w, F visit
     int iy = min(max(int(floorf(w.p[1])), 0), g.ny - 1);
     int iz = min(max(int(floorf(w.p[2])), 0), g.nz - 1);
     const int sx = w.h[0] > 0.0f ? 1 : -1, sy = w.h[1] > 0.0f ? 1 : -1, sz = w.h[2] > 0.0f ? 1 : -1;
+    int off = base + ix + iy * ystride + iz * zstride;
+    const int ox = sx, oy = sy * ystride, oz = sz * zstride;
     // distance from p to the first crossing of an axis (voxel i), and between crossings
     auto first = [](float p, int i, float h) {
         return h > 0.0f ? (float(i + 1) - p) / h : (h < 0.0f ? (p - float(i)) / -h : 3.0e38f);
@@ -107,7 +112,7 @@ __device__ __forceinline__ void walk(const GeomDev &g, const RayWalk &w, F visit
     const int max_steps = g.nx + g.ny + g.nz + 3;
     for (int n = 0; n < max_steps; ++n) {
         const float dt = fminf(dx, fminf(dy, dz));
-        visit(ix, iy, iz, fmaxf(dt, 0.0f) * g.vox);
+        visit(off, fmaxf(dt, 0.0f));
         // the axis crossed first steps (ties go to x, then y); the others move
         // dt closer to their next crossing.  Selects instead of branches: the
         // lanes of a warp cross different axes, and a three-way branch would
@@ -116,6 +121,7 @@ __device__ __forceinline__ void walk(const GeomDev &g, const RayWalk &w, F visit
         ix += mx ? sx : 0;
         iy += my ? sy : 0;
         iz += mz ? sz : 0;
+        off += mx ? ox : (my ? oy : oz);
         dx = mx ? tdx : dx - dt;
         dy = my ? tdy : dy - dt;
         dz = mz ? tdz : dz - dt;
@@ -138,13 +144,14 @@ __global__ void __launch_bounds__(256) siddon_A_kernel(GeomDev g, const float *_
     RayWalk w;
     float acc = 0.0f;
     if (ray_walk(g, s, iv, iu, w)) {
-        walk(g, w, [&](int ix, int iy, int iz, float len) {
-            const size_t e = (size_t(iz + PAD_A) * g.ny + iy) * g.pitchY + ix + PAD_A;
+        // Yc[zp][y][xp]: voxel (ix, iy, iz) at (iz + PAD_A) ny pitchY + iy pitchY + ix + PAD_A
+        const int ystride = g.pitchY, zstride = g.ny * g.pitchY;
+        walk(g, w, PAD_A * zstride + PAD_A, ystride, zstride, [&](int e, float len) {
             const float v = BF ? bf16_lo(__ldg(reinterpret_cast<const uint32_t *>(Yc) + e)) : __ldg(Yc + e);
             acc = fmaf(v, len, acc);
         });
     }
-    store_sino(y, lay, s, iv, iu, acc);
+    store_sino(y, lay, s, iv, iu, acc * g.vox);
 }
 
 __global__ void __launch_bounds__(256) siddon_At_kernel(GeomDev g, const float *__restrict__ y,
@@ -161,8 +168,10 @@ __global__ void __launch_bounds__(256) siddon_At_kernel(GeomDev g, const float *
     const int iv = rem / g.nu, iu = rem - iv * g.nu;
     RayWalk w;
     if (!ray_walk(g, s, iv, iu, w)) return;
-    walk(g, w, [&](int ix, int iy, int iz, float len) {
-        if (len > 0.0f) atomicAdd(x + (size_t(iz) * g.ny + iy) * g.nx + ix, yr * len);
+    // lengths come in voxel units: the ray's value carries the voxel size
+    const float yv = yr * g.vox;
+    walk(g, w, 0, g.nx, g.nx * g.ny, [&](int e, float len) {
+        if (len > 0.0f) atomicAdd(x + e, yv * len);
     });
 }
 
