@@ -118,9 +118,13 @@ CONE_THIN = _cone("cone_thin", 0, 2.5, 36, 50, 7, 3.5, nxyz=(30, 26, 5), ang0=0.
 PAR2D_ANISO = Geometry(name="par2d_aniso", kind=PARALLEL_2D, nx=37, ny=29, nz=1,
                        vox=1.3, n_views=41, ang0=0.1, span=math.pi, nu=53, nv=1,
                        du=1.1, dv=1.0)
+# 40 slices: the last 16-slice run of the bf16 back-projector passes nz by 8
+# slices (the row margin must cover them), while 8-slice runs end at nz
+CONE_Z40 = _cone("cone_z40", 40, 3.0, 48, 66, 44, 4.5, ang0=0.15)
 
 WORKLOADS = {g.name: g for g in (PAR2D_64, CONE_128, CONE_256, CONE_512, CONE_512_CUT64,
-                                 CONE_GRAD32, CONE_SMALL, CONE_ANISO, CONE_THIN, PAR2D_ANISO)}
+                                 CONE_GRAD32, CONE_SMALL, CONE_ANISO, CONE_THIN, PAR2D_ANISO,
+                                 CONE_Z40)}
 
 
 def scaled(g: Geometry, **kw) -> Geometry:

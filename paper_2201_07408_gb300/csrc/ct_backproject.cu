@@ -544,8 +544,6 @@ __global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_2pass_kernel(GeomDev g
     }
 }
 
-constexpr int B_ZC_2PASS = 16;
-
 template <int ZC, bool BF>
 static cudaError_t launch_voxel_B_2pass(const GeomDev &g, const float *ypad, float *x, const int *stop,
                                         cudaStream_t st)

@@ -138,14 +138,14 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     // back-projector row margin: a voxel at height z projects to row
     // cv + M z/dv with M <= sdd/(sod - r_max); pad so that the floor of that
     // and the row above stay inside the zero-bordered buffer, for every
-    // slice the threads compute (runs of B_ZC slices up to a multiple of
-    // B_ZC past nz)
+    // slice the threads compute (runs of up to B_ZC_RUN_MAX slices, so up
+    // to a multiple of B_ZC_RUN_MAX past nz)
     int padv = PAD_V;
     if (d->kind == CT_CONE_3D) {
         const double vx = d->voxel_mm;
         const double rmax = std::sqrt(std::pow(0.5 * (d->nx - 1) * vx, 2) + std::pow(0.5 * (d->ny - 1) * vx, 2));
         const double mmax = d->sdd_mm / (d->sod_mm - rmax);
-        const int nz_run = d->nz == 1 ? 1 : (d->nz + B_ZC - 1) / B_ZC * B_ZC;
+        const int nz_run = d->nz == 1 ? 1 : (d->nz + B_ZC_RUN_MAX - 1) / B_ZC_RUN_MAX * B_ZC_RUN_MAX;
         const double zslices = std::max(0.5 * (d->nz - 1), nz_run - 1 - 0.5 * (d->nz - 1));
         const double over = zslices * vx * mmax / d->dv_mm - 0.5 * (d->nv - 1);
         padv = std::max(PAD_V, int(std::ceil(std::max(over, 0.0))) + PAD_V);

@@ -31,13 +31,16 @@ constexpr int PAD_V = 2;   // rows, above and below each view
 constexpr int A_VR = CT_A_VR;
 constexpr int AT_VR = CT_AT_VR;
 constexpr int A_VR_MAX = A_VR > AT_VR ? A_VR : AT_VR;
-// consecutive z slices per back-projector thread (3D); the last run of a
+// consecutive z slices per back-projector thread (3D): B_ZC for FP32 quads,
+// B_ZC_2PASS for the two-pass kernel on bf16 quads.  The last run of a
 // column may pass nz: those slices are computed and discarded, and the
-// padded sinogram's row margin covers them too
+// padded sinogram's row margin covers them too (sized for B_ZC_RUN_MAX).
 #ifndef CT_B_ZC
 #define CT_B_ZC 8
 #endif
 constexpr int B_ZC = CT_B_ZC;
+constexpr int B_ZC_2PASS = 16;
+constexpr int B_ZC_RUN_MAX = B_ZC > B_ZC_2PASS ? B_ZC : B_ZC_2PASS;
 
 
 // Per-view constants of the projector, from which a ray's direction, its

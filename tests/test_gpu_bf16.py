@@ -66,7 +66,7 @@ def test_project_A_bf16_volume(ct, spec):
     assert rel(y.cpu().numpy(), ref) <= 1e-5
 
 
-@pytest.mark.parametrize("spec", [ci.CONE_SMALL, ci.CONE_ANISO, ci.PAR2D_ANISO], ids=lambda s: s.name)
+@pytest.mark.parametrize("spec", [ci.CONE_SMALL, ci.CONE_ANISO, ci.CONE_Z40, ci.PAR2D_ANISO], ids=lambda s: s.name)
 @pytest.mark.parametrize("b_kind", ["un", "fbp"])
 def test_backproject_B_bf16_sinogram(ct, spec, b_kind):
     g = ct.Geometry.from_spec(spec, sino_dtype="bf16")
