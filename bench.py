@@ -213,13 +213,13 @@ NCU_TRAFFIC = {
     # (kernel, storage, workload): (bytes per launch, source file,
     # sha256 of that file followed by ct_internal.cuh at capture time)
     ("voxel_B", "f32", "cone_256"): (1415970560 + 68444672, "ct_backproject.cu",
-                                     "eb55300ae338b650fe939231e067489d998d264a067d1a05ef292821fde63500"),
+                                     "01642bb8190c5eb32582cc007609ca3866daa0bc19d611ab86f1c20c4ae78602"),
     ("voxel_B", "bf16", "cone_256"): (565138944 + 61659392, "ct_backproject.cu",
-                                      "eb55300ae338b650fe939231e067489d998d264a067d1a05ef292821fde63500"),
+                                      "01642bb8190c5eb32582cc007609ca3866daa0bc19d611ab86f1c20c4ae78602"),
     ("joseph_A", "f32", "cone_256"): (410601984 + 137186816, "ct_project.cu",
-                                      "e5c36ae4139e92ca3bfb2cb308078c2cb0ad1adacb65c5a41e47c0f5fe3c6304"),
+                                      "f3d9d23f1a744617c05e296b8a7e307903d3f87e900863f50edce8770f2a3acc"),
     ("joseph_A", "bf16", "cone_256"): (429411840 + 153559040, "ct_project.cu",
-                                       "e5c36ae4139e92ca3bfb2cb308078c2cb0ad1adacb65c5a41e47c0f5fe3c6304"),
+                                       "f3d9d23f1a744617c05e296b8a7e307903d3f87e900863f50edce8770f2a3acc"),
 }
 
 
