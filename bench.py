@@ -213,9 +213,9 @@ NCU_TRAFFIC = {
     # (kernel, storage, workload): (bytes per launch, source file,
     # sha256 of that file followed by ct_internal.cuh at capture time)
     ("voxel_B", "f32", "cone_256"): (1415970560 + 68444672, "ct_backproject.cu",
-                                     "01642bb8190c5eb32582cc007609ca3866daa0bc19d611ab86f1c20c4ae78602"),
+                                     "3c04c3c123042c2d27467272b5fc00877bcbe9308090dcd35220e8f45ef0d1bf"),
     ("voxel_B", "bf16", "cone_256"): (565138944 + 61659392, "ct_backproject.cu",
-                                      "01642bb8190c5eb32582cc007609ca3866daa0bc19d611ab86f1c20c4ae78602"),
+                                      "3c04c3c123042c2d27467272b5fc00877bcbe9308090dcd35220e8f45ef0d1bf"),
     ("joseph_A", "f32", "cone_256"): (410601984 + 137186816, "ct_project.cu",
                                       "f3d9d23f1a744617c05e296b8a7e307903d3f87e900863f50edce8770f2a3acc"),
     ("joseph_A", "bf16", "cone_256"): (429411840 + 153559040, "ct_project.cu",

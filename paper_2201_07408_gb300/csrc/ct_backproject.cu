@@ -696,20 +696,18 @@ __global__ void __launch_bounds__(B_TILE *B_TILE) voxel_Bt_run_kernel(GeomDev g,
                 vc = v0;
                 acc_lo = c_lo;
                 acc_hi = c_hi;
-            } else if (v0 == vc) {
-                acc_lo += c_lo;
-                acc_hi += c_hi;
-            } else if (v0 == vc + 1) {   // row vc is complete
-                flush(vc, acc_lo);
+            } else {
+                // the run stays on row vc, moves to vc + 1 (row vc is complete)
+                // or skips a row (rows vc and vc + 1 are complete).  The two
+                // flushes are shared by the lanes that need them and the
+                // sums are selected, so lanes in different cases do not run
+                // separate copies of the atomics.
+                const bool same = v0 == vc, next = v0 == vc + 1;
+                if (!same) flush(vc, acc_lo);
+                if (!same && !next) flush(vc + 1, acc_hi);
+                acc_lo = same ? acc_lo + c_lo : (next ? acc_hi + c_lo : c_lo);
+                acc_hi = same ? acc_hi + c_hi : c_hi;
                 vc = v0;
-                acc_lo = acc_hi + c_lo;
-                acc_hi = c_hi;
-            } else {                     // the run skipped a row
-                flush(vc, acc_lo);
-                flush(vc + 1, acc_hi);
-                vc = v0;
-                acc_lo = c_lo;
-                acc_hi = c_hi;
             }
         }
         flush(vc, acc_lo);
