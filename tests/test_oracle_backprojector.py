@@ -167,3 +167,62 @@ def test_fbp_reconstructs_ball_density_cone():
     Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
     inner = (X ** 2 + Y ** 2 + Z ** 2) < 15.0 ** 2
     assert abs(f[inner].mean() - 1.0) < 0.05
+
+
+def ray_obliquity(g, s, iu, iv):
+    """Cosine of the angle between the ray from the source to pixel (iu, iv)
+    of view s and the central ray, from the scan's vectors: source
+    S = sod (c, s, 0), detector centre D = -(sdd - sod) (c, s, 0), pixel
+    P = D + u e_u + v e_v with e_u = (-s, c, 0), e_v = (0, 0, 1)."""
+    th = g.ang0 + s * g.span / g.n_views
+    c, sn = math.cos(th), math.sin(th)
+    S = g.sod * np.array([c, sn, 0.0])
+    D = -(g.sdd - g.sod) * np.array([c, sn, 0.0])
+    u = (iu - (g.nu - 1) / 2.0) * g.du
+    v = (iv - (g.nv - 1) / 2.0) * g.dv
+    d = D + u * np.array([-sn, c, 0.0]) + v * np.array([0.0, 0.0, 1.0]) - S
+    central = D - S
+    return float(d @ central) / (np.linalg.norm(d) * np.linalg.norm(central))
+
+
+@pytest.mark.parametrize("g", [ci.CONE_SMALL, ci.CONE_ANISO], ids=lambda g: g.name)
+def test_ramp_cosine_weight_from_ray_geometry(g):
+    """F = c_F tau H diag(w) with w the cosine of each ray's angle to the
+    central ray (FDK weighting, the reading of Sec. III's ramp filter); F^T
+    applies w after the convolution.  A unit impulse at pixel (k, iv) is
+    filtered into c_F tau h[i - k] w(k, iv) along its row: every output
+    divided by w(k, iv) is the same kernel whatever the pixel, the corners
+    included (w ~ 0.985 there), and it equals the ramp kernel's centre
+    value c_F tau / (4 tau^2) at i = k.  For F^T each output i carries
+    w(i, iv) instead.  w is computed here from the source and pixel
+    positions, not from the oracle's closed form."""
+    tau = g.du * g.sod / g.sdd
+    centre = oracle.ramp_scale(g) / (4.0 * tau * tau)
+    s = 3
+    rows = sorted({0, g.nv // 2, g.nv - 1})
+    cols = sorted({0, 1, g.nu // 2, g.nu - 2, g.nu - 1})
+    kernels = {}
+    w_min = 1.0
+    for iv in rows:
+        for k in cols:
+            e = np.zeros(g.sino_shape)
+            e[s, iv, k] = 1.0
+            f = oracle.ramp_F(g, e)[s, iv]
+            ft = oracle.ramp_Ft(g, e)[s, iv]
+            others = np.delete(oracle.ramp_F(g, e).reshape(g.n_views * g.nv, g.nu), s * g.nv + iv, axis=0)
+            assert not np.any(others), "F mixes detector rows"
+            wk = ray_obliquity(g, s, k, iv)
+            wi = np.array([ray_obliquity(g, s, i, iv) for i in range(g.nu)])
+            w_min = min(w_min, wk)
+            assert abs(f[k] - centre * wk) <= 1e-13 * centre
+            # the kernel seen from pixel k: h[d] for d = i - k
+            for i in range(g.nu):
+                d = i - k
+                hd = f[i] / wk
+                assert abs(ft[i] - hd * wi[i]) <= 1e-13 * centre, ("F^T weight", iv, k, i)
+                if d in kernels:
+                    assert abs(hd - kernels[d]) <= 1e-13 * centre, ("F weight", iv, k, i)
+                else:
+                    kernels[d] = hd
+    # the corners are oblique enough that a missing or misplaced weight shows
+    assert w_min < 0.99
