@@ -279,6 +279,66 @@ CT_API ct_status ct_mgs_sweep(const float *V_dev, size_t ldv, int j, size_t len,
 CT_API ct_status ct_basis_combine(const float *V_dev, size_t ldv, int k, size_t len,
                            const double *y_dev, float *x_dev, void *stream);
 
+/* Persistent BA-GMRES state: a solve whose workspace outlives the call, so
+ * that it can be extended by more iterations, saved to a file and restored
+ * later.  The paper stores the growing Krylov basis on disk and adds one
+ * vector per iteration (Sec. II); here the basis stays in device memory, or
+ * in page-locked host memory (CT_BASIS_HOST) that the kernels read and write
+ * in place, on Grace-Blackwell over NVLink-C2C, for bases larger than the
+ * device memory left free.  Iterating a state k times gives bit for bit the
+ * image and residual history of ct_bagmres_solve with k iterations and the
+ * same options, however the k iterations are split over calls, saved and
+ * restored.  opts->tol is ignored (a state runs the iterations it is asked
+ * for); opts->workspace is ignored (the state allocates its own memory with
+ * cudaMalloc, and cudaHostAlloc for a host basis).  A state belongs to its
+ * geometry (which must outlive it) and to the device that was current when
+ * it was made; it is not safe for concurrent use. */
+typedef struct ct_gmres_state ct_gmres_state;
+typedef enum { CT_BASIS_DEVICE = 0, CT_BASIS_HOST = 1 } ct_basis_location;
+
+/* Allocates a state for up to kmax iterations (1..4096) of BA-GMRES on
+ * `geom` with opts->b_kind, dot_mode and reorth (NULL = defaults), its basis
+ * of kmax+1 image vectors at `basis`.  CT_ENOMEM when an allocation fails. */
+CT_API ct_status ct_bagmres_state_create(const ct_geom *geom, int kmax, int basis, const ct_solve_opts *opts,
+                                         ct_gmres_state **out);
+
+/* Starts (or restarts) the solve from x0 = 0 with data b_dev (m floats):
+ * r0 = B b, resid[0] = ||B b||.  Stream-ordered, asynchronous. */
+CT_API ct_status ct_bagmres_state_start(ct_gmres_state *state, const float *b_dev, void *stream);
+
+/* Runs the iterations from the state's current count up to k (1 <= k <=
+ * kmax; none when k is not above the count) and writes x_k = V_k y_k to
+ * x_out_dev (n floats); with k below the count it forms the earlier iterate
+ * x_k from the first k basis vectors.  resid_hist: HOST array of k+1
+ * doubles, as in ct_bagmres_solve (may be NULL).  iters_done: the index of
+ * the iterate written (k, or fewer after a lucky breakdown).  Synchronous.
+ * Return codes as ct_bagmres_solve. */
+CT_API ct_status ct_bagmres_state_extend(ct_gmres_state *state, int k, float *x_out_dev, double *resid_hist,
+                                         int *iters_done, void *stream);
+
+/* Iterations done by the state as of its last synchronous call (-1 for NULL). */
+CT_API int ct_gmres_state_iters(const ct_gmres_state *state);
+
+/* Bytes of the basis of a state with capacity kmax on `geom`. */
+CT_API size_t ct_gmres_state_basis_bytes(const ct_geom *geom, int kmax);
+
+/* Writes the state (the basis vectors of the iterations done, the Hessenberg
+ * and rotated columns, the rotations, g, the residual history, the pending
+ * Krylov vector, the device status and the geometry description) to `path`
+ * in a binary file that ct_gmres_state_load reads on any machine of the same
+ * byte order.  Waits for `stream` first.  CT_EINVAL when the file cannot be
+ * written or the state was never started. */
+CT_API ct_status ct_gmres_state_save(const ct_gmres_state *state, const char *path, void *stream);
+
+/* Restores a saved state into a new one of capacity kmax (>= the iterations
+ * saved) with its basis at `basis`.  The geometry must equal the saved one
+ * (CT_EINVAL otherwise).  Synchronous. */
+CT_API ct_status ct_gmres_state_load(const ct_geom *geom, const char *path, int kmax, int basis,
+                                     ct_gmres_state **out, void *stream);
+
+/* Frees the state (waits for the device first).  NULL is a no-op. */
+CT_API void ct_gmres_state_destroy(ct_gmres_state *state);
+
 /* Size in bytes of the fixed device scratch of ct_project_A_noalloc. */
 #define CT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 
@@ -318,6 +378,38 @@ CT_API void ct_profile_enable(int on);
 CT_API void ct_profile_reset(void);
 CT_API int ct_profile_read(double *ms_out, long long *launches_out, int max_kinds);
 CT_API const char *ct_profile_kind_name(int kind);
+
+/* Ceiling of the SM load path that the gather kernels (A, B) use: the best
+ * of `repeats` timed launches (after one warm-up) of a kernel in which every
+ * block reads its own 16 KiB window, resident in its SM's L1 after the
+ * first pass, with 128-bit read-only loads (lanes on consecutive words),
+ * over and over.  *gbs_out receives the bytes loaded per second / 1e9.
+ * Instrumentation for the roofline (no counterpart in the paper).  Takes a
+ * few MiB from the stream-ordered allocator on `stream`; synchronous.
+ * CT_EINVAL for repeats < 1 or gbs_out NULL; CT_ECUDA on a CUDA failure. */
+CT_API ct_status ct_measure_gather_peak(int repeats, double *gbs_out, void *stream);
+
+/* Host-side fault injection, for testing the failure paths of a caller
+ * without a GPU fault (no counterpart in the paper).  `spec` is a
+ * comma-separated list of
+ *   "nan_at_iter:N"  every later solve writes a NaN (an ordinary value, by a
+ *                    one-thread kernel) into the new Krylov vector of
+ *                    iteration N >= 1 (GMRES), or into q = A p (CGLS), so it
+ *                    returns CT_ENONFINITE with iters_done = N - 1, the
+ *                    residual history valid up to N - 1 and -1 after;
+ *   "oom"            every later request to the stream-ordered allocator is
+ *                    refused as if it had failed (CT_ENOMEM); calls given a
+ *                    workspace, and ct_project_A_noalloc, still run;
+ *   "none" or ""     (or spec NULL) clears the injection.
+ * The environment variable CT_FAULT, read once when the library is loaded,
+ * sets the initial spec (a malformed value is reported on stderr and
+ * ignored).  Process-wide.  Returns CT_EINVAL, leaving the active spec
+ * unchanged, for a malformed spec. */
+CT_API ct_status ct_fault_set(const char *spec);
+
+/* The active fault spec in canonical form ("" when none), valid until the
+ * calling thread's next call. */
+CT_API const char *ct_fault_get(void);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 CT_API const char *ct_last_error(void);

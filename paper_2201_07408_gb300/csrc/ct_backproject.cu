@@ -743,6 +743,7 @@ using namespace ct;
 extern "C" ct_status ct_ramp_F(const ct_geom *geom, const float *y_dev, float *yf_dev, int transpose,
                                void *stream)
 {
+    NvtxRange call_range("ct_ramp_F");
     if (!geom || !y_dev || !yf_dev) return set_error(CT_EINVAL, "ct_ramp_F: NULL argument");
     if (y_dev == yf_dev) return set_error(CT_EINVAL, "ct_ramp_F: input and output must differ");
     cudaError_t e = launch_ramp(geom->g, y_dev, yf_dev, plain_layout(geom->g), transpose != 0, nullptr,
@@ -754,6 +755,7 @@ extern "C" ct_status ct_ramp_F(const ct_geom *geom, const float *y_dev, float *y
 extern "C" ct_status ct_backproject_B(const ct_geom *geom, const float *y_dev, float *x_dev, int b_kind,
                                       void *stream)
 {
+    NvtxRange call_range("ct_backproject_B");
     if (!geom || !y_dev || !x_dev) return set_error(CT_EINVAL, "ct_backproject_B: NULL argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (b_kind == CT_B_AT) return ct_adjoint_At(geom, y_dev, x_dev, stream);
@@ -780,6 +782,7 @@ extern "C" ct_status ct_backproject_B(const ct_geom *geom, const float *y_dev, f
 extern "C" ct_status ct_adjoint_Bt(const ct_geom *geom, const float *x_dev, float *y_dev, int b_kind,
                                    void *stream)
 {
+    NvtxRange call_range("ct_adjoint_Bt");
     if (!geom || !x_dev || !y_dev) return set_error(CT_EINVAL, "ct_adjoint_Bt: NULL argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (b_kind == CT_B_AT) return ct_project_A(geom, x_dev, y_dev, stream);

@@ -44,6 +44,8 @@ ct_status arena_open(Arena &a, size_t bytes, void *workspace, size_t workspace_b
         a.owned = false;
         return CT_OK;
     }
+    if (fault_spec().oom)
+        return set_error(CT_ENOMEM, "cudaMallocAsync(%zu bytes) refused: fault injected by CT_FAULT=oom", bytes);
     void *p = nullptr;
     cudaError_t e = cudaMallocAsync(&p, bytes, stream);
     if (e != cudaSuccess) {

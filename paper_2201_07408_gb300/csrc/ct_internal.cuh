@@ -3,6 +3,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cstddef>
 #include <cstdint>
 
@@ -289,6 +290,25 @@ cudaError_t launch_voxel_Bt(const GeomDev &g, const float *x, float *y, const in
 
 // --- vector kernels (ct_krylov.cu) ---------------------------------------------
 int num_sms();
+
+// --- host-side fault injection (ct_fault.cu; CT_FAULT, ct_fault_set) --------------
+struct FaultSpec {
+    int nan_at_iter = 0;   // iteration (>= 1) whose new vector gets a NaN; 0 = off
+    int oom = 0;           // refuse stream-ordered allocations
+};
+FaultSpec fault_spec();
+// Writes a NaN into v[0] when the spec names this iteration (1-based).
+cudaError_t fault_poison(float *v, int iteration, const int *stop, cudaStream_t st);
+
+// --- NVTX ranges: one per C-ABI call and per solver iteration ---------------------
+// (host-side markers around the launches; free when no tool is attached)
+class NvtxRange {
+public:
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // --- optional per-kernel timing (ct_profile.cu) ----------------------------------
 enum ProfKind {

@@ -17,6 +17,9 @@
 #include <cmath>
 #include <mutex>
 #include <unordered_map>
+#include <cstdio>
+#include <cstring>
+#include <new>
 #include <vector>
 
 #include "ct_internal.cuh"
@@ -474,6 +477,9 @@ __global__ void givens_kernel(int j, int k, double *H, const double *H2, double 
 // *cnt = j when iterate j exists (j <= iterations done), else 0
 __global__ void iterate_count_kernel(const SolverState *st, int j, int *cnt) { *cnt = j <= st->iters ? j : 0; }
 
+// *cnt = min(k, iterations done): the iterate x_k, or the last one when fewer exist
+__global__ void iterate_upto_kernel(const SolverState *st, int k, int *cnt) { *cnt = st->iters < k ? st->iters : k; }
+
 // y = R_j^{-1} g_j for the first *cnt columns: the least-squares coefficients
 // of iterate x_j (R's first j columns and g's first j entries are final once
 // iteration j is done)
@@ -704,14 +710,25 @@ struct GmresWs {
     void *vec(int i) { return static_cast<char *>(V) + size_t(i) * ldv * (vbf16 ? 2 : 4); }
 };
 
-static bool carve_gmres(Arena &ar, const GeomDev &g, int k, bool ab, int b_kind, GmresWs &w)
+// Bytes of the k+1 basis vectors of a BA (ab = false) or AB workspace.
+static size_t basis_bytes(const GeomDev &g, int k, bool ab)
+{
+    const size_t len = ab ? size_t(g.n_views) * g.nv * g.nu : size_t(g.nx) * g.ny * g.nz;
+    return Arena::align(round_ld(len) * size_t(k + 1) * ((!ab && g.vol_bf16) ? 2 : 4));
+}
+
+// external_basis: the basis lives elsewhere (w.V is set by the caller)
+static bool carve_gmres(Arena &ar, const GeomDev &g, int k, bool ab, int b_kind, GmresWs &w,
+                        bool external_basis = false)
 {
     const size_t n = size_t(g.nx) * g.ny * g.nz;
     const size_t m = size_t(g.n_views) * g.nv * g.nu;
     const size_t len = ab ? m : n;
     w.ldv = round_ld(len);
     w.vbf16 = !ab && g.vol_bf16;
-    if (w.vbf16)
+    if (external_basis)
+        w.V = nullptr;
+    else if (w.vbf16)
         w.V = ar.take<__nv_bfloat16>(w.ldv * size_t(k + 1));
     else
         w.V = ar.take<float>(w.ldv * size_t(k + 1));
@@ -735,13 +752,13 @@ static bool carve_gmres(Arena &ar, const GeomDev &g, int k, bool ab, int b_kind,
     return w.st != nullptr;
 }
 
-static size_t gmres_bytes(const GeomDev &g, int k, bool ab, int b_kind)
+static size_t gmres_bytes(const GeomDev &g, int k, bool ab, int b_kind, bool external_basis = false)
 {
     Arena ar;
     ar.size = ~size_t(0) >> 1;
     ar.base = nullptr;
     GmresWs w;
-    carve_gmres(ar, g, k, ab, b_kind, w);
+    carve_gmres(ar, g, k, ab, b_kind, w, external_basis);
     return ar.used;
 }
 
@@ -753,7 +770,7 @@ static cudaError_t arnoldi_orthogonalise(GmresWs &w, float *q, int j, int k, siz
     const int *stop = &w.st->status;
     unsigned *ctr = &w.st->counter;
     double *hcol = w.H + size_t(j) * (k + 1);
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = fault_poison(q, j + 1, stop, s);
     for (int i = 0; i <= j + 1 && e == cudaSuccess; ++i) {
         const void *vprev = i > 0 ? w.vec(i - 1) : nullptr;
         const double *hprev = i > 0 ? hcol + (i - 1) : nullptr;
@@ -808,6 +825,51 @@ static ct_status open_ws(Arena &ar, size_t bytes, const ct_solve_opts &o, cudaSt
 // ---------------------------------------------------------------------------
 // BA-GMRES
 // ---------------------------------------------------------------------------
+// BA-GMRES in three steps, shared by the one-call solve and the persistent
+// solver state (kmax: the workspace's capacity, the leading dimension of H).
+//
+// Start (x0 = 0): r0 = B b into q; ||r0|| starts the residual history.
+static cudaError_t ba_start(const GeomDev &g, GmresWs &w, const float *b, int kmax, size_t n,
+                            const ct_solve_opts &o, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(w.st, 0, sizeof(SolverState), s);
+    // zero the padded sinogram once: its border is never written afterwards
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(w.ob.ypad, 0, padded_sino_floats(g) * sizeof(float), s);
+    if (e == cudaSuccess)
+        e = apply_B(g, o.b_kind, const_cast<float *>(b), nullptr, false, w.ob, w.q, nullptr, s, nullptr);
+    if (e == cudaSuccess)
+        e = mgs_pass(o.dot_mode, w.q, nullptr, nullptr, nullptr, n, w.partials, &w.st->counter, nullptr,
+                     &w.st->sumsq, nullptr, nullptr, s);
+    if (e == cudaSuccess) {
+        { ProfScope prof(PK_SMALL, s); gmres_init_kernel<<<1, 1, 0, s>>>(w.st, w.g, w.resid, kmax); }
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+// Iteration j (0-based): v_j = q / ||q|| joins the basis, q = B A v_j is
+// orthogonalised against v_0..v_j, and the Givens step updates the residual.
+static cudaError_t ba_iteration(const GeomDev &g, GmresWs &w, int j, int kmax, size_t n, const ct_solve_opts &o,
+                                cudaStream_t s)
+{
+    NvtxRange iter_range("BA-GMRES iteration");
+    const int *stop = &w.st->status;
+    // v_j = q / ||q|| stored in the basis while the projector's plane copies are built
+    cudaError_t e = launch_plane_copies(g, w.q, &w.st->inv_norm, w.vec(j), w.ob.Xc, w.ob.Yc, stop, s);
+    if (e != cudaSuccess) return e;
+    // q = B A v_j
+    if (o.b_kind == CT_B_UN) {
+        e = launch_project_A(g, w.ob.Xc, w.ob.Yc, w.ob.ypad, padded_layout(g), stop, s);
+        if (e == cudaSuccess) e = launch_voxel_B(g, w.ob.ypad, w.q, stop, s, QUAD_CORNERS);
+    } else {
+        e = launch_project_A(g, w.ob.Xc, w.ob.Yc, w.ob.t, plain_layout(g), stop, s);
+        if (e == cudaSuccess) e = apply_B(g, o.b_kind, w.ob.t, nullptr, false, w.ob, w.q, stop, s, nullptr);
+    }
+    if (e == cudaSuccess) e = arnoldi_orthogonalise(w, w.q, j, kmax, n, o, s);
+    return e;
+}
+
 static ct_status bagmres(const ct_geom *geom, const float *b, int k, float *x, double *resid_hist,
                          const ct_solve_opts &o, int *iters_done, cudaStream_t s, const float *x_ref = nullptr,
                          double *err_hist = nullptr)
@@ -819,35 +881,8 @@ static ct_status bagmres(const ct_geom *geom, const float *b, int k, float *x, d
     if (rc != CT_OK) return rc;
     GmresWs w;
     carve_gmres(ar, g, k, false, o.b_kind, w);
-    const int *stop = &w.st->status;
-    cudaError_t e = cudaMemsetAsync(w.st, 0, sizeof(SolverState), s);
-    // zero the padded sinogram once: its border is never written afterwards
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(w.ob.ypad, 0, padded_sino_floats(g) * sizeof(float), s);
-    // r0 = B b -> q; its norm starts the residual history
-    if (e == cudaSuccess)
-        e = apply_B(g, o.b_kind, const_cast<float *>(b), nullptr, false, w.ob, w.q, nullptr, s, nullptr);
-    if (e == cudaSuccess)
-        e = mgs_pass(o.dot_mode, w.q, nullptr, nullptr, nullptr, n, w.partials, &w.st->counter, nullptr,
-                     &w.st->sumsq, nullptr, nullptr, s);
-    if (e == cudaSuccess) {
-        { ProfScope prof(PK_SMALL, s); gmres_init_kernel<<<1, 1, 0, s>>>(w.st, w.g, w.resid, k); }
-        e = cudaGetLastError();
-    }
-    for (int j = 0; j < k && e == cudaSuccess; ++j) {
-        // v_j = q / ||q|| stored in the basis while the projector's plane copies are built
-        e = launch_plane_copies(g, w.q, &w.st->inv_norm, w.vec(j), w.ob.Xc, w.ob.Yc, stop, s);
-        if (e != cudaSuccess) break;
-        // q = B A v_j
-        if (o.b_kind == CT_B_UN) {
-            e = launch_project_A(g, w.ob.Xc, w.ob.Yc, w.ob.ypad, padded_layout(g), stop, s);
-            if (e == cudaSuccess) e = launch_voxel_B(g, w.ob.ypad, w.q, stop, s, QUAD_CORNERS);
-        } else {
-            e = launch_project_A(g, w.ob.Xc, w.ob.Yc, w.ob.t, plain_layout(g), stop, s);
-            if (e == cudaSuccess) e = apply_B(g, o.b_kind, w.ob.t, nullptr, false, w.ob, w.q, stop, s, nullptr);
-        }
-        if (e == cudaSuccess) e = arnoldi_orthogonalise(w, w.q, j, k, n, o, s);
-    }
+    cudaError_t e = ba_start(g, w, b, k, n, o, s);
+    for (int j = 0; j < k && e == cudaSuccess; ++j) e = ba_iteration(g, w, j, k, n, o, s);
     // distance of every iterate x_j = V_j y_j to x_ref (x_out is the scratch
     // image; the final x_k is formed after)
     if (x_ref && e == cudaSuccess) {
@@ -991,6 +1026,7 @@ static ct_status abgmres(const ct_geom *geom, const float *b, int k, float *x, d
         e = cudaGetLastError();
     }
     for (int j = 0; j < k && e == cudaSuccess; ++j) {
+        NvtxRange iter_range("AB-GMRES iteration");
         float *vj = Vf + size_t(j) * w.ldv;
         float *q = Vf + size_t(j + 1) * w.ldv;
         e = apply_B(g, o.b_kind, vj, &w.st->inv_norm, true, w.ob, w.tvol, stop, s, nullptr);
@@ -1109,6 +1145,7 @@ static ct_status bagmres_vjp(const ct_geom *geom, const float *gx, int k, float 
         e = cudaGetLastError();
     }
     for (int j = 0; j < k && e == cudaSuccess; ++j) {
+        NvtxRange iter_range("adjoint GMRES iteration");
         float *vj = Vf + size_t(j) * gm.ldv;
         float *q = Vf + size_t(j + 1) * gm.ldv;
         {
@@ -1201,9 +1238,11 @@ static ct_status cgls(const ct_geom *geom, const float *b, int k, float *x, doub
         e = cudaGetLastError();
     }
     for (int j = 1; j <= k && e == cudaSuccess; ++j) {
+        NvtxRange iter_range("CGLS iteration");
         // q = A p ; delta = ||q||^2
         e = launch_plane_copies(g, w.p, nullptr, nullptr, w.ob.Xc, w.ob.Yc, stop, s);
         if (e == cudaSuccess) e = launch_project_A(g, w.ob.Xc, w.ob.Yc, w.q, plain_layout(g), stop, s);
+        if (e == cudaSuccess) e = fault_poison(w.q, j, stop, s);
         if (e == cudaSuccess)
             e = mgs_pass(1, w.q, nullptr, nullptr, nullptr, m, w.partials, ctr, nullptr, &st->delta, stop, nullptr, s);
         if (e == cudaSuccess) {
@@ -1248,6 +1287,114 @@ static ct_status cgls(const ct_geom *geom, const float *b, int k, float *x, doub
     return rc;
 }
 
+// ---------------------------------------------------------------------------
+// Persistent BA-GMRES state: the workspace of one solve kept between calls,
+// so a finished solve can be extended by more iterations, saved to a file
+// and restored (the paper keeps its growing Krylov basis on disk, Sec. II).
+// The basis lives in device memory or in page-locked host memory that the
+// kernels read and write in place (on Grace-Blackwell over NVLink-C2C).
+// ---------------------------------------------------------------------------
+struct StateFileHeader {
+    char magic[8];            // "CTGMRS01"
+    int version;              // 1
+    int vbf16;                // basis storage: 1 = bf16, 0 = float
+    ct_geom_desc desc;        // the geometry the state belongs to
+    int b_kind, dot_mode, reorth;
+    int k_done;               // iterations done
+    unsigned long long n;     // basis vector length
+    SolverState st;           // device solver state at the save
+};
+
+}  // namespace ct
+
+struct ct_gmres_state {
+    const ct_geom *geom = nullptr;
+    ct_solve_opts o{};
+    int kmax = 0;
+    int basis = CT_BASIS_DEVICE;
+    void *dev_mem = nullptr;      // cudaMalloc'ed workspace (all but a host basis)
+    void *host_basis = nullptr;   // cudaHostAlloc'ed basis (CT_BASIS_HOST)
+    ct::GmresWs w;
+    int started = 0;
+    int k_done = 0;               // iterations done, as of the last synchronising call
+    int status = 0;               // device status word, as of the last synchronising call
+};
+
+namespace ct {
+
+static void state_free(ct_gmres_state *st)
+{
+    if (!st) return;
+    if (st->dev_mem) cudaFree(st->dev_mem);
+    if (st->host_basis) cudaFreeHost(st->host_basis);
+    delete st;
+}
+
+static ct_status state_alloc(const ct_geom *geom, int kmax, int basis, const ct_solve_opts &o, ct_gmres_state **out)
+{
+    const GeomDev &g = geom->g;
+    const bool host = basis == CT_BASIS_HOST;
+    ct_gmres_state *st = new (std::nothrow) ct_gmres_state;
+    if (!st) return set_error(CT_ENOMEM, "ct_bagmres_state: out of host memory");
+    st->geom = geom;
+    st->o = o;
+    st->o.tol = 0.0;   // the state runs exactly the iterations asked for
+    st->o.workspace = nullptr;
+    st->o.workspace_bytes = 0;
+    st->kmax = kmax;
+    st->basis = basis;
+    const size_t bytes = gmres_bytes(g, kmax, false, o.b_kind, host);
+    cudaError_t e = cudaMalloc(&st->dev_mem, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        st->dev_mem = nullptr;
+        state_free(st);
+        return set_error(CT_ENOMEM, "ct_bagmres_state: cudaMalloc(%zu bytes) failed", bytes);
+    }
+    Arena ar;
+    ar.base = static_cast<char *>(st->dev_mem);
+    ar.size = bytes;
+    carve_gmres(ar, g, kmax, false, o.b_kind, st->w, host);
+    if (host) {
+        const size_t vb = basis_bytes(g, kmax, false);
+        e = cudaHostAlloc(&st->host_basis, vb, cudaHostAllocMapped | cudaHostAllocPortable);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            st->host_basis = nullptr;
+            state_free(st);
+            return set_error(CT_ENOMEM, "ct_bagmres_state: cudaHostAlloc(%zu bytes) for the basis failed", vb);
+        }
+        void *dp = nullptr;
+        e = cudaHostGetDevicePointer(&dp, st->host_basis, 0);
+        if (e != cudaSuccess) {
+            state_free(st);
+            return cuda_error(e, "cudaHostGetDevicePointer(basis)");
+        }
+        st->w.V = dp;
+    }
+    *out = st;
+    return CT_OK;
+}
+
+static ct_status state_check_device(const ct_geom *geom, const char *who)
+{
+    int dev = -1;
+    CT_CUDA(cudaGetDevice(&dev));
+    if (dev != geom->device)
+        return set_error(CT_EINVAL, "%s: the geometry lives on device %d but device %d is current", who,
+                         geom->device, dev);
+    return CT_OK;
+}
+
+static bool same_desc(const ct_geom_desc &a, const ct_geom_desc &b)
+{
+    return a.kind == b.kind && a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.voxel_mm == b.voxel_mm &&
+           a.n_views == b.n_views && a.angle_start_rad == b.angle_start_rad &&
+           a.angle_span_rad == b.angle_span_rad && a.nu == b.nu && a.nv == b.nv && a.du_mm == b.du_mm &&
+           a.dv_mm == b.dv_mm && a.sod_mm == b.sod_mm && a.sdd_mm == b.sdd_mm && a.vol_dtype == b.vol_dtype &&
+           a.sino_dtype == b.sino_dtype && a.projector == b.projector;
+}
+
 }  // namespace ct
 
 using namespace ct;
@@ -1278,6 +1425,7 @@ size_t ct_workspace_bytes(const ct_geom *geom, int k, int solver, const ct_solve
 ct_status ct_bagmres_solve(const ct_geom *geom, const float *b_dev, int k, float *x_out_dev,
                            double *resid_hist, const ct_solve_opts *opts, int *iters_done, void *stream)
 {
+    NvtxRange call_range("ct_bagmres_solve");
     ct_solve_opts o = resolve_opts(opts);
     ct_status rc = check_common(geom, b_dev, k, x_out_dev, &o);
     if (rc != CT_OK) return rc;
@@ -1287,6 +1435,7 @@ ct_status ct_bagmres_solve(const ct_geom *geom, const float *b_dev, int k, float
 ct_status ct_bagmres_solve_host(const ct_geom *geom, const float *b_host, int k, float *x_out_host,
                                 double *resid_hist, const ct_solve_opts *opts, int *iters_done, void *stream)
 {
+    NvtxRange call_range("ct_bagmres_solve_host");
     ct_solve_opts o = resolve_opts(opts);
     ct_status rc = check_common(geom, b_host, k, x_out_host, &o);
     if (rc != CT_OK) return rc;
@@ -1319,6 +1468,7 @@ ct_status ct_bagmres_solve_err(const ct_geom *geom, const float *b_dev, int k, f
                                const float *x_ref_dev, double *resid_hist, double *err_hist,
                                const ct_solve_opts *opts, int *iters_done, void *stream)
 {
+    NvtxRange call_range("ct_bagmres_solve_err");
     ct_solve_opts o = resolve_opts(opts);
     ct_status rc = check_common(geom, b_dev, k, x_out_dev, &o);
     if (rc != CT_OK) return rc;
@@ -1330,6 +1480,7 @@ ct_status ct_bagmres_solve_err(const ct_geom *geom, const float *b_dev, int k, f
 ct_status ct_bagmres_restarted(const ct_geom *geom, const float *b_dev, int m, int cycles, float *x_out_dev,
                                double *resid_hist, const ct_solve_opts *opts, int *iters_done, void *stream)
 {
+    NvtxRange call_range("ct_bagmres_restarted");
     ct_solve_opts o = resolve_opts(opts);
     ct_status rc = check_common(geom, b_dev, m, x_out_dev, &o);
     if (rc != CT_OK) return rc;
@@ -1342,6 +1493,7 @@ ct_status ct_bagmres_restarted(const ct_geom *geom, const float *b_dev, int m, i
 ct_status ct_abgmres_solve(const ct_geom *geom, const float *b_dev, int k, float *x_out_dev,
                            double *resid_hist, const ct_solve_opts *opts, int *iters_done, void *stream)
 {
+    NvtxRange call_range("ct_abgmres_solve");
     ct_solve_opts o = resolve_opts(opts);
     ct_status rc = check_common(geom, b_dev, k, x_out_dev, &o);
     if (rc != CT_OK) return rc;
@@ -1351,6 +1503,7 @@ ct_status ct_abgmres_solve(const ct_geom *geom, const float *b_dev, int k, float
 ct_status ct_cgls_solve(const ct_geom *geom, const float *b_dev, int k, float *x_out_dev,
                         double *resid_hist, const ct_solve_opts *opts, int *iters_done, void *stream)
 {
+    NvtxRange call_range("ct_cgls_solve");
     ct_solve_opts o = resolve_opts(opts);
     ct_status rc = check_common(geom, b_dev, k, x_out_dev, &o);
     if (rc != CT_OK) return rc;
@@ -1360,6 +1513,7 @@ ct_status ct_cgls_solve(const ct_geom *geom, const float *b_dev, int k, float *x
 ct_status ct_bagmres_vjp(const ct_geom *geom, const float *gx_dev, int k, float *gb_dev, double *resid_hist,
                          const ct_solve_opts *opts, int *iters_done, void *stream)
 {
+    NvtxRange call_range("ct_bagmres_vjp");
     ct_solve_opts o = resolve_opts(opts);
     if (!geom || !gx_dev || !gb_dev) return set_error(CT_EINVAL, "ct_bagmres_vjp: NULL argument");
     if (k < 1 || k > 4096) return set_error(CT_EINVAL, "ct_bagmres_vjp: k must be in [1, 4096] (got %d)", k);
@@ -1368,9 +1522,263 @@ ct_status ct_bagmres_vjp(const ct_geom *geom, const float *gx_dev, int k, float 
     return bagmres_vjp(geom, gx_dev, k, gb_dev, resid_hist, o, iters_done, static_cast<cudaStream_t>(stream));
 }
 
+ct_status ct_bagmres_state_create(const ct_geom *geom, int kmax, int basis, const ct_solve_opts *opts,
+                                  ct_gmres_state **out)
+{
+    NvtxRange call_range("ct_bagmres_state_create");
+    if (out) *out = nullptr;
+    if (!geom || !out) return set_error(CT_EINVAL, "ct_bagmres_state_create: NULL argument");
+    if (kmax < 1 || kmax > 4096)
+        return set_error(CT_EINVAL, "ct_bagmres_state_create: kmax must be in 1..4096 (got %d)", kmax);
+    if (basis != CT_BASIS_DEVICE && basis != CT_BASIS_HOST)
+        return set_error(CT_EINVAL, "ct_bagmres_state_create: unknown basis location %d", basis);
+    ct_solve_opts o = resolve_opts(opts);
+    if (o.b_kind != CT_B_UN && o.b_kind != CT_B_FBP && o.b_kind != CT_B_AT)
+        return set_error(CT_EINVAL, "ct_bagmres_state_create: unknown b_kind %d", o.b_kind);
+    if (o.dot_mode != 0 && o.dot_mode != 1)
+        return set_error(CT_EINVAL, "ct_bagmres_state_create: dot_mode must be 0 or 1");
+    ct_status rc = state_check_device(geom, "ct_bagmres_state_create");
+    if (rc != CT_OK) return rc;
+    return state_alloc(geom, kmax, basis, o, out);
+}
+
+void ct_gmres_state_destroy(ct_gmres_state *state)
+{
+    if (!state) return;
+    cudaDeviceSynchronize();   // no kernel of the state may still run
+    state_free(state);
+}
+
+int ct_gmres_state_iters(const ct_gmres_state *state) { return state ? state->k_done : -1; }
+
+size_t ct_gmres_state_basis_bytes(const ct_geom *geom, int kmax)
+{
+    if (!geom || kmax < 1) return 0;
+    return basis_bytes(geom->g, kmax, false);
+}
+
+ct_status ct_bagmres_state_start(ct_gmres_state *state, const float *b_dev, void *stream)
+{
+    NvtxRange call_range("ct_bagmres_state_start");
+    if (!state || !b_dev) return set_error(CT_EINVAL, "ct_bagmres_state_start: NULL argument");
+    ct_status rc = state_check_device(state->geom, "ct_bagmres_state_start");
+    if (rc != CT_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = ba_start(state->geom->g, state->w, b_dev, state->kmax, state->geom->n, state->o, s);
+    if (e != cudaSuccess) return cuda_error(e, "ct_bagmres_state_start launch");
+    state->started = 1;
+    state->k_done = 0;
+    state->status = ST_RUN;
+    return CT_OK;
+}
+
+ct_status ct_bagmres_state_extend(ct_gmres_state *state, int k, float *x_out_dev, double *resid_hist,
+                                  int *iters_done, void *stream)
+{
+    NvtxRange call_range("ct_bagmres_state_extend");
+    if (!state || !x_out_dev) return set_error(CT_EINVAL, "ct_bagmres_state_extend: NULL argument");
+    if (!state->started) return set_error(CT_EINVAL, "ct_bagmres_state_extend: the state has not been started");
+    if (k < 1 || k > state->kmax)
+        return set_error(CT_EINVAL, "ct_bagmres_state_extend: k must be in 1..%d (the state's kmax), got %d",
+                         state->kmax, k);
+    ct_status rc = state_check_device(state->geom, "ct_bagmres_state_extend");
+    if (rc != CT_OK) return rc;
+    const GeomDev &g = state->geom->g;
+    const size_t n = state->geom->n;
+    GmresWs &w = state->w;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (state->status == ST_RUN)
+        for (int j = state->k_done; j < k && e == cudaSuccess; ++j) e = ba_iteration(g, w, j, state->kmax, n, state->o, s);
+    // x = V_c y_c with c = min(k, iterations done)
+    if (e == cudaSuccess) {
+        ProfScope prof(PK_SMALL, s);
+        iterate_upto_kernel<<<1, 1, 0, s>>>(w.st, k, w.cnt);
+        backsolve_count_kernel<<<1, 1, 0, s>>>(w.R, w.g, w.y, w.cnt, state->kmax);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = w.vbf16 ? combine_t(static_cast<const __nv_bfloat16 *>(w.V), w.ldv, state->kmax, n, w.y, w.cnt,
+                                x_out_dev, s)
+                    : combine(static_cast<const float *>(w.V), w.ldv, state->kmax, n, w.y, w.cnt, x_out_dev, s);
+    if (e != cudaSuccess) return cuda_error(e, "ct_bagmres_state_extend launch");
+    SolverState hst;
+    std::vector<double> hres(size_t(k) + 1);
+    CT_CUDA(cudaMemcpyAsync(&hst, w.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    CT_CUDA(cudaMemcpyAsync(hres.data(), w.resid, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, s));
+    CT_CUDA(cudaStreamSynchronize(s));
+    state->k_done = hst.iters;
+    state->status = hst.status;
+    if (resid_hist) std::copy(hres.begin(), hres.end(), resid_hist);
+    if (iters_done) *iters_done = hst.iters < k ? hst.iters : k;
+    if (hst.status == ST_NONFINITE)
+        return set_error(CT_ENONFINITE, "ct_bagmres_state_extend: a norm became NaN/Inf after %d iterations",
+                         hst.iters);
+    if (hst.status == ST_LUCKY) return CT_BREAKDOWN_LUCKY;
+    return CT_OK;
+}
+
+ct_status ct_gmres_state_save(const ct_gmres_state *state, const char *path, void *stream)
+{
+    NvtxRange call_range("ct_gmres_state_save");
+    if (!state || !path) return set_error(CT_EINVAL, "ct_gmres_state_save: NULL argument");
+    if (!state->started) return set_error(CT_EINVAL, "ct_gmres_state_save: the state has not been started");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const GmresWs &w = state->w;
+    const size_t n = state->geom->n;
+    const int kd = state->k_done;
+    const size_t ld = size_t(state->kmax) + 1;
+    StateFileHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "CTGMRS01", 8);
+    h.version = 1;
+    h.vbf16 = w.vbf16 ? 1 : 0;
+    h.desc = state->geom->desc;
+    h.b_kind = state->o.b_kind;
+    h.dot_mode = state->o.dot_mode;
+    h.reorth = state->o.reorth;
+    h.k_done = kd;
+    h.n = n;
+    CT_CUDA(cudaStreamSynchronize(s));
+    CT_CUDA(cudaMemcpy(&h.st, w.st, sizeof(SolverState), cudaMemcpyDeviceToHost));
+    if (h.st.iters != kd) return set_error(CT_EINVAL, "ct_gmres_state_save: the state changed since its last call");
+    // the first kd columns of H and R (rows 0..kd), cs, sn, g and resid (kd + 1)
+    const size_t rows = size_t(kd) + 1;
+    std::vector<double> H(rows * kd), R(rows * kd), cs(kd), sn(kd), gv(rows), res(rows);
+    for (int j = 0; j < kd; ++j) {
+        CT_CUDA(cudaMemcpy(H.data() + j * rows, w.H + j * ld, rows * sizeof(double), cudaMemcpyDeviceToHost));
+        CT_CUDA(cudaMemcpy(R.data() + j * rows, w.R + j * ld, rows * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    if (kd > 0) {
+        CT_CUDA(cudaMemcpy(cs.data(), w.cs, kd * sizeof(double), cudaMemcpyDeviceToHost));
+        CT_CUDA(cudaMemcpy(sn.data(), w.sn, kd * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    CT_CUDA(cudaMemcpy(gv.data(), w.g, rows * sizeof(double), cudaMemcpyDeviceToHost));
+    CT_CUDA(cudaMemcpy(res.data(), w.resid, rows * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<float> q(n);
+    CT_CUDA(cudaMemcpy(q.data(), w.q, n * sizeof(float), cudaMemcpyDeviceToHost));
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return set_error(CT_EINVAL, "ct_gmres_state_save: cannot open %s for writing", path);
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+    auto put = [&](const void *p, size_t bytes) { ok = ok && (bytes == 0 || std::fwrite(p, bytes, 1, f) == 1); };
+    put(H.data(), H.size() * sizeof(double));
+    put(R.data(), R.size() * sizeof(double));
+    put(cs.data(), cs.size() * sizeof(double));
+    put(sn.data(), sn.size() * sizeof(double));
+    put(gv.data(), gv.size() * sizeof(double));
+    put(res.data(), res.size() * sizeof(double));
+    put(q.data(), n * sizeof(float));
+    // the kd basis vectors, one at a time
+    const size_t esz = w.vbf16 ? 2 : 4;
+    std::vector<char> vbuf(n * esz);
+    for (int i = 0; i < kd && ok; ++i) {
+        cudaError_t e = cudaMemcpy(vbuf.data(), w.vec(i), n * esz, cudaMemcpyDefault);
+        if (e != cudaSuccess) {
+            std::fclose(f);
+            return cuda_error(e, "ct_gmres_state_save: basis copy");
+        }
+        put(vbuf.data(), n * esz);
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return set_error(CT_EINVAL, "ct_gmres_state_save: writing %s failed", path);
+    return CT_OK;
+}
+
+ct_status ct_gmres_state_load(const ct_geom *geom, const char *path, int kmax, int basis, ct_gmres_state **out,
+                              void *stream)
+{
+    NvtxRange call_range("ct_gmres_state_load");
+    if (out) *out = nullptr;
+    if (!geom || !path || !out) return set_error(CT_EINVAL, "ct_gmres_state_load: NULL argument");
+    if (basis != CT_BASIS_DEVICE && basis != CT_BASIS_HOST)
+        return set_error(CT_EINVAL, "ct_gmres_state_load: unknown basis location %d", basis);
+    ct_status rc = state_check_device(geom, "ct_gmres_state_load");
+    if (rc != CT_OK) return rc;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return set_error(CT_EINVAL, "ct_gmres_state_load: cannot open %s", path);
+    StateFileHeader h;
+    bool ok = std::fread(&h, sizeof(h), 1, f) == 1;
+    const size_t n = geom->n;
+    if (!ok || std::memcmp(h.magic, "CTGMRS01", 8) != 0 || h.version != 1) {
+        std::fclose(f);
+        return set_error(CT_EINVAL, "ct_gmres_state_load: %s is not a saved solver state", path);
+    }
+    if (!same_desc(h.desc, geom->desc) || h.n != n || h.vbf16 != (geom->g.vol_bf16 ? 1 : 0)) {
+        std::fclose(f);
+        return set_error(CT_EINVAL, "ct_gmres_state_load: %s belongs to another geometry", path);
+    }
+    const int kd = h.k_done;
+    if (kd < 0 || kd > 4096 || kmax < kd || kmax < 1 || kmax > 4096) {
+        std::fclose(f);
+        return set_error(CT_EINVAL, "ct_gmres_state_load: kmax %d must be in %d..4096 (the iterations saved)",
+                         kmax, kd > 1 ? kd : 1);
+    }
+    ct_solve_opts o;
+    ct_solve_opts_default(&o);
+    o.b_kind = h.b_kind;
+    o.dot_mode = h.dot_mode;
+    o.reorth = h.reorth;
+    ct_gmres_state *st = nullptr;
+    rc = state_alloc(geom, kmax, basis, o, &st);
+    if (rc != CT_OK) {
+        std::fclose(f);
+        return rc;
+    }
+    const size_t rows = size_t(kd) + 1, ld = size_t(kmax) + 1;
+    std::vector<double> H(rows * kd), R(rows * kd), cs(kd), sn(kd), gv(rows), res(rows);
+    auto get = [&](void *p, size_t bytes) { ok = ok && (bytes == 0 || std::fread(p, bytes, 1, f) == 1); };
+    get(H.data(), H.size() * sizeof(double));
+    get(R.data(), R.size() * sizeof(double));
+    get(cs.data(), cs.size() * sizeof(double));
+    get(sn.data(), sn.size() * sizeof(double));
+    get(gv.data(), gv.size() * sizeof(double));
+    get(res.data(), res.size() * sizeof(double));
+    std::vector<float> q(n);
+    get(q.data(), n * sizeof(float));
+    GmresWs &w = st->w;
+    cudaError_t e = cudaSuccess;
+    // H, R, g zero beyond what was saved; resid -1 after the iterations done
+    std::vector<double> res_full(ld, -1.0);
+    std::copy(res.begin(), res.end(), res_full.begin());
+    e = cudaMemset(w.H, 0, sizeof(double) * ld * kmax);
+    if (e == cudaSuccess) e = cudaMemset(w.R, 0, sizeof(double) * ld * kmax);
+    if (e == cudaSuccess) e = cudaMemset(w.g, 0, sizeof(double) * ld);
+    if (e == cudaSuccess) e = cudaMemset(w.ob.ypad, 0, padded_sino_floats(geom->g) * sizeof(float));
+    for (int j = 0; j < kd && e == cudaSuccess; ++j) {
+        e = cudaMemcpy(w.H + j * ld, H.data() + j * rows, rows * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(w.R + j * ld, R.data() + j * rows, rows * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess && kd > 0) e = cudaMemcpy(w.cs, cs.data(), kd * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && kd > 0) e = cudaMemcpy(w.sn, sn.data(), kd * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(w.g, gv.data(), rows * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(w.resid, res_full.data(), ld * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(w.q, q.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(w.st, &h.st, sizeof(SolverState), cudaMemcpyHostToDevice);
+    const size_t esz = w.vbf16 ? 2 : 4;
+    std::vector<char> vbuf(n * esz);
+    for (int i = 0; i < kd && ok && e == cudaSuccess; ++i) {
+        get(vbuf.data(), n * esz);
+        if (ok) e = cudaMemcpy(w.vec(i), vbuf.data(), n * esz, cudaMemcpyDefault);
+    }
+    std::fclose(f);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (!ok || e != cudaSuccess) {
+        state_free(st);
+        if (e != cudaSuccess) return cuda_error(e, "ct_gmres_state_load: upload");
+        return set_error(CT_EINVAL, "ct_gmres_state_load: %s is truncated", path);
+    }
+    st->started = 1;
+    st->k_done = kd;
+    st->status = h.st.status;
+    *out = st;
+    return CT_OK;
+}
+
 ct_status ct_mgs_sweep(const float *V_dev, size_t ldv, int j, size_t len, float *q_dev, double *h_dev,
                        int dot_mode, void *stream)
 {
+    NvtxRange call_range("ct_mgs_sweep");
     if (!q_dev || !h_dev || (j > 0 && !V_dev)) return set_error(CT_EINVAL, "ct_mgs_sweep: NULL argument");
     if (j < 0 || len == 0 || (j > 0 && ldv < len))
         return set_error(CT_EINVAL, "ct_mgs_sweep: bad sizes (j=%d len=%zu ldv=%zu)", j, len, ldv);
@@ -1404,6 +1812,7 @@ ct_status ct_mgs_sweep(const float *V_dev, size_t ldv, int j, size_t len, float 
 ct_status ct_basis_combine(const float *V_dev, size_t ldv, int k, size_t len, const double *y_dev,
                            float *x_dev, void *stream)
 {
+    NvtxRange call_range("ct_basis_combine");
     if (!V_dev || !y_dev || !x_dev) return set_error(CT_EINVAL, "ct_basis_combine: NULL argument");
     if (k < 1 || len == 0 || ldv < len) return set_error(CT_EINVAL, "ct_basis_combine: bad sizes");
     if (k > 4096) return set_error(CT_EINVAL, "ct_basis_combine: k must be <= 4096");

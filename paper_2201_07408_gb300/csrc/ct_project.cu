@@ -567,6 +567,7 @@ using namespace ct;
 
 extern "C" ct_status ct_project_A(const ct_geom *geom, const float *x_dev, float *y_dev, void *stream)
 {
+    NvtxRange call_range("ct_project_A");
     if (!geom || !x_dev || !y_dev) return set_error(CT_EINVAL, "ct_project_A: NULL argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const GeomDev &g = geom->g;
@@ -584,6 +585,7 @@ extern "C" ct_status ct_project_A(const ct_geom *geom, const float *x_dev, float
 
 extern "C" ct_status ct_adjoint_At(const ct_geom *geom, const float *y_dev, float *x_dev, void *stream)
 {
+    NvtxRange call_range("ct_adjoint_At");
     if (!geom || !y_dev || !x_dev) return set_error(CT_EINVAL, "ct_adjoint_At: NULL argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const GeomDev &g = geom->g;

@@ -76,6 +76,17 @@ SIGNATURES = {
     "ct_profile_reset": (None, []),
     "ct_profile_read": (_i, [_P(_d), _P(ctypes.c_longlong), _i]),
     "ct_profile_kind_name": (ctypes.c_char_p, [_i]),
+    "ct_measure_gather_peak": (_i, [_i, _P(_d), _vp]),
+    "ct_bagmres_state_create": (_i, [_vp, _i, _i, _P(ct_solve_opts), _P(_vp)]),
+    "ct_bagmres_state_start": (_i, [_vp, _vp, _vp]),
+    "ct_bagmres_state_extend": (_i, [_vp, _i, _vp, _P(_d), _P(_i), _vp]),
+    "ct_gmres_state_iters": (_i, [_vp]),
+    "ct_gmres_state_basis_bytes": (_sz, [_vp, _i]),
+    "ct_gmres_state_save": (_i, [_vp, ctypes.c_char_p, _vp]),
+    "ct_gmres_state_load": (_i, [_vp, ctypes.c_char_p, _i, _i, _P(_vp), _vp]),
+    "ct_gmres_state_destroy": (None, [_vp]),
+    "ct_fault_set": (_i, [ctypes.c_char_p]),
+    "ct_fault_get": (ctypes.c_char_p, []),
     "ct_last_error": (ctypes.c_char_p, []),
     "ct_version": (ctypes.c_char_p, []),
 }
@@ -100,15 +111,20 @@ def lib():
 
 
 class CTError(RuntimeError):
-    def __init__(self, name, status):
+    """A C-ABI call returned an error status.  For a solver, ``result`` holds
+    what the call reported before it stopped (iterations done and the residual
+    history, -1 after the last iteration done), else None."""
+
+    def __init__(self, name, status, result=None):
         self.status = status
+        self.result = result
         msg = lib().ct_last_error().decode(errors="replace")
         super().__init__("%s failed with %s: %s" % (name, STATUS_NAMES.get(status, status), msg))
 
 
-def _check(name, status, allow=(CT_OK,)):
+def _check(name, status, allow=(CT_OK,), result=None):
     if status not in allow:
-        raise CTError(name, status)
+        raise CTError(name, status, result)
     return status
 
 
@@ -286,8 +302,9 @@ def _solve(name, fn, solver, geom, b, k, x_out, opts, stream, workspace):
     st = fn(geom.handle, _ptr(b, geom.m, "b", d), int(k), _ptr(x_out, geom.n, "x_out", d),
             resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opts), ctypes.byref(iters),
             _stream(stream, d))
-    _check(name, st, allow=(CT_OK, CT_BREAKDOWN_LUCKY))
-    return SolveResult(status=st, iters=iters.value, resid=resid)
+    out = SolveResult(status=st, iters=iters.value, resid=resid)
+    _check(name, st, allow=(CT_OK, CT_BREAKDOWN_LUCKY), result=out)
+    return out
 
 
 def ct_bagmres_solve(geom, b, k, x_out, opts=None, stream=None, workspace="torch") -> SolveResult:
@@ -313,8 +330,9 @@ def ct_bagmres_solve_host(geom, b_host, k, x_out_host, opts=None, stream=None, w
                                      _host_ptr(x_out_host, geom.n, "x_out_host"),
                                      resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opts),
                                      ctypes.byref(iters), _stream(stream, d))
-    _check("ct_bagmres_solve_host", st, allow=(CT_OK, CT_BREAKDOWN_LUCKY))
-    return SolveResult(status=st, iters=iters.value, resid=resid)
+    out = SolveResult(status=st, iters=iters.value, resid=resid)
+    _check("ct_bagmres_solve_host", st, allow=(CT_OK, CT_BREAKDOWN_LUCKY), result=out)
+    return out
 
 
 def _torch_workspace(geom, k, solver, opts):
@@ -392,8 +410,73 @@ def ct_bagmres_vjp(geom, gx, k, gb_out, opts=None, stream=None, workspace="torch
     st = lib().ct_bagmres_vjp(geom.handle, _ptr(gx, geom.n, "gx", d), int(k), _ptr(gb_out, geom.m, "gb", d),
                               resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opts),
                               ctypes.byref(iters), _stream(stream, d))
-    _check("ct_bagmres_vjp", st, allow=(CT_OK, CT_BREAKDOWN_LUCKY))
-    return SolveResult(status=st, iters=iters.value, resid=resid)
+    out = SolveResult(status=st, iters=iters.value, resid=resid)
+    _check("ct_bagmres_vjp", st, allow=(CT_OK, CT_BREAKDOWN_LUCKY), result=out)
+    return out
+
+
+CT_BASIS_DEVICE, CT_BASIS_HOST = 0, 1
+
+
+class GmresState:
+    """A persistent BA-GMRES solve (ct_bagmres_state_*): start(b), then
+    extend(k) as often as wanted; save(path) / GmresState.load(...)."""
+
+    def __init__(self, geom: "Geometry", kmax: int, basis="device", opts=None, _handle=None):
+        self.geom = geom
+        self.kmax = int(kmax)
+        self.basis = CT_BASIS_HOST if basis in ("host", CT_BASIS_HOST) else CT_BASIS_DEVICE
+        if _handle is not None:
+            self._h = _handle
+            return
+        h = ctypes.c_void_p()
+        _check("ct_bagmres_state_create",
+               lib().ct_bagmres_state_create(geom.handle, self.kmax, self.basis,
+                                             ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def load(cls, geom, path, kmax, basis="device", stream=None):
+        h = ctypes.c_void_p()
+        b = CT_BASIS_HOST if basis in ("host", CT_BASIS_HOST) else CT_BASIS_DEVICE
+        _check("ct_gmres_state_load", lib().ct_gmres_state_load(geom.handle, str(path).encode(), int(kmax), b,
+                                                                 ctypes.byref(h), _stream(stream, geom.device)))
+        return cls(geom, kmax, b, _handle=h)
+
+    def start(self, b, stream=None):
+        d = self.geom.device
+        _check("ct_bagmres_state_start", lib().ct_bagmres_state_start(self._h, _ptr(b, self.geom.m, "b", d),
+                                                                      _stream(stream, d)))
+
+    def extend(self, k, x_out, stream=None) -> SolveResult:
+        d = self.geom.device
+        resid = np.zeros(int(k) + 1, dtype=np.float64)
+        iters = ctypes.c_int(0)
+        st = lib().ct_bagmres_state_extend(self._h, int(k), _ptr(x_out, self.geom.n, "x_out", d),
+                                           resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           ctypes.byref(iters), _stream(stream, d))
+        out = SolveResult(status=st, iters=iters.value, resid=resid)
+        _check("ct_bagmres_state_extend", st, allow=(CT_OK, CT_BREAKDOWN_LUCKY), result=out)
+        return out
+
+    @property
+    def iters(self) -> int:
+        return int(lib().ct_gmres_state_iters(self._h))
+
+    def save(self, path, stream=None):
+        _check("ct_gmres_state_save", lib().ct_gmres_state_save(self._h, str(path).encode(),
+                                                                _stream(stream, self.geom.device)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ct_gmres_state_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ct_mgs_sweep(V, ldv, j, length, q, h, dot_mode=0, stream=None):
@@ -433,6 +516,25 @@ def profile_read():
     cnt = (ctypes.c_longlong * n)()
     k = lib().ct_profile_read(ms, cnt, n)
     return {lib().ct_profile_kind_name(i).decode(): (ms[i], int(cnt[i])) for i in range(min(k, n))}
+
+
+def measure_gather_peak(repeats=5, stream=None, device=None):
+    """GB/s of the SM load path's ceiling (ct_measure_gather_peak)."""
+    d = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    out = ctypes.c_double(0.0)
+    _check("ct_measure_gather_peak", lib().ct_measure_gather_peak(int(repeats), ctypes.byref(out),
+                                                                  _stream(stream, d)))
+    return out.value
+
+
+def fault_set(spec):
+    """Sets the host-side fault injection (ct_fault_set): "nan_at_iter:N",
+    "oom", a comma-separated list, or None / "" / "none" to clear."""
+    _check("ct_fault_set", lib().ct_fault_set(None if spec is None else spec.encode()))
+
+
+def fault_get() -> str:
+    return lib().ct_fault_get().decode()
 
 
 def version() -> str:

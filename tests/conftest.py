@@ -28,3 +28,26 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture
+def parity_log(request):
+    """Returns log(**fields): appends one JSON line (the test id and the
+    fields) to the file named by the environment variable CT_PARITY_REPORT,
+    when it is set.  The solver tests record through it, per case, the
+    iteration count, the oracle's own sensitivity, the tolerance in force and
+    the error the GPU reached, so the tolerances can be audited case by
+    case."""
+    import json
+
+    path = os.environ.get("CT_PARITY_REPORT")
+
+    def log(**fields):
+        if not path:
+            return
+        rec = {"test": request.node.nodeid}
+        rec.update({k: (float(v) if hasattr(v, "dtype") else v) for k, v in fields.items()})
+        with open(path, "a") as f:
+            f.write(json.dumps(rec) + "\n")
+
+    return log

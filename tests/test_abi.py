@@ -80,3 +80,36 @@ def test_null_arguments_are_rejected(libct):
     assert L.ct_bagmres_solve(None, None, 5, None, None, None, None, None) == libct.CT_EINVAL
     assert L.ct_workspace_bytes(None, 5, 0, None) == 0
     L.ct_geom_destroy(None)
+
+
+@pytest.mark.parametrize("spec,canon", [("nan_at_iter:5", "nan_at_iter:5"), ("oom", "oom"),
+                                        ("oom,nan_at_iter:12", "nan_at_iter:12,oom"), ("none", ""), ("", "")])
+def test_fault_spec_parsing(libct, spec, canon):
+    L = libct.lib()
+    assert L.ct_fault_set(spec.encode()) == libct.CT_OK
+    assert L.ct_fault_get().decode() == canon
+    assert L.ct_fault_set(None) == libct.CT_OK and L.ct_fault_get() == b""
+
+
+@pytest.mark.parametrize("bad", ["nan_at_iter:0", "nan_at_iter:", "nan_at_iter:x", "nan_at_iter:3x", "segv",
+                                 "oom,,bogus"])
+def test_fault_spec_rejects_malformed(libct, bad):
+    L = libct.lib()
+    assert L.ct_fault_set(b"oom") == libct.CT_OK
+    assert L.ct_fault_set(bad.encode()) == libct.CT_EINVAL
+    assert b"ct_fault_set" in L.ct_last_error()
+    assert L.ct_fault_get() == b"oom"          # unchanged
+    L.ct_fault_set(None)
+
+
+@pytest.mark.parametrize("env,canon,warns", [("nan_at_iter:7", "nan_at_iter:7", False), ("bogus", "", True)])
+def test_fault_spec_from_environment(libct, env, canon, warns):
+    import subprocess
+    import sys
+    code = ("import ctypes; L = ctypes.CDLL(%r); L.ct_fault_get.restype = ctypes.c_char_p; "
+            "print(L.ct_fault_get().decode())" % libct.LIB_PATH)
+    r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, CT_FAULT=env), capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == canon
+    assert ("ignoring CT_FAULT" in r.stderr) == warns

@@ -3,15 +3,24 @@ building blocks against the FP64 oracle, through the C-ABI.
 
 Tolerances: the reconstructed image and the residual history after k
 iterations agree with the FP64 oracle to relative error <= 1e-4 (residuals
-relative to resid[0]), or, where the k-th iterate is more sensitive than
-that to FP32 operator error, to 3x the oracle's own sensitivity: the oracle
-is run a second time with every operator output perturbed by a seeded
-relative error of 1e-6 (the class of the FP32 operators' error, which the
-operator tests bound by 1e-5 and measure at ~3e-7 to 7e-7), and its
-deviation d_k from the unperturbed run (computed by the oracle alone) is
-what an FP32 implementation can be expected to reach at iteration k; near a
-stagnation of GMRES on noisy data d_k reaches 1e-2.  Full-size solves are
-checked through properties that hold at any size.
+relative to resid[0]).  The cases listed in EXCEPTIONS are held instead to
+3x the oracle's own sensitivity: the oracle is run a second time with every
+operator output perturbed by a seeded relative error of 1e-6 (the class of
+the FP32 operators' error, which the operator tests bound by 1e-5 and
+measure at ~3e-7 to 7e-7), and its deviation d_k from the unperturbed run
+(computed by the oracle alone) is what an FP32 implementation can be
+expected to reach at iteration k.  Each exception records its measured d_k
+and GPU error, and whether a variant of the solver (plain FP32 dot
+products, a second MGS sweep) meets the flat bar; where one does, that
+variant is held to 1e-4 in the same test.  Full-size solves are
+checked through properties that hold at any size, and against the oracle's
+stored solves in tests/test_gpu_large.py.
+
+Every parity case records, through the ``parity_log`` fixture (a JSON line
+per case when CT_PARITY_REPORT names a file): k, d_img and d_res, the
+tolerances in force and the GPU's errors.  Where a GPU error is above the
+flat 1e-4, the case also records the errors of the solve rerun with plain
+FP32 dot products (dot_mode = 1) and with a second MGS sweep (reorth = 1).
 """
 import numpy as np
 import pytest
@@ -24,6 +33,21 @@ from oracle import krylov
 pytestmark = pytest.mark.gpu
 
 SOLVE_TOL = 1e-4
+
+# (solver, scan, b_kind, k, dot_mode) -> why the k-th iterate is held to 3 d_k
+# rather than 1e-4 (measured on a GB300: d = the oracle's sensitivity to a
+# 1e-6 operator perturbation, err = the GPU's distance to the oracle), and
+# the solver variant, if any, that meets 1e-4 on the same case.
+EXCEPTIONS = {
+    ("ba", "par2d_64", "un", 30, 0): dict(
+        why="noisy 2D scan, 30 iterations past the semi-convergence minimum: d_img = 5.9e-4, "
+            "GPU image error 1.1e-4 with compensated dots and one MGS sweep",
+        flat_with="reorth=1"),   # measured 4.4e-5 with the second sweep
+    ("ab", "par2d_64", "un", 20, 0): dict(
+        why="AB-GMRES image x = B y_20 on the noisy 2D scan: d_img = 8.9e-3, GPU image error 8.9e-3 "
+            "(the same with plain dots or a second sweep, 8.9e-3); residual history within 1e-4",
+        flat_with=None),
+}
 
 
 @pytest.fixture(scope="module")
@@ -59,6 +83,48 @@ def _perturbed(f, rng):
     return g
 
 
+class Sensitive:
+    """An FP64 oracle solve with its sensitivity: ``ref`` the oracle's
+    result, ``d_img`` = ||x_pert - x|| / ||x|| and ``d_res`` =
+    max_j |r_pert[j] - r[j]| / r[0] for the oracle rerun with FP32-class
+    (1e-6) operator error; ``sens_x``, ``sens_r`` = max(1e-4, 3 d), the
+    tolerances of a listed exception."""
+
+    def __init__(self, ref, d_img, d_res, key="resid"):
+        self.ref, self.d_img, self.d_res, self.key = ref, float(d_img), float(d_res), key
+        self.sens_x = max(SOLVE_TOL, 3 * self.d_img)
+        self.sens_r = max(SOLVE_TOL, 3 * self.d_res)
+
+    def errors(self, x_gpu, resid_gpu):
+        r = self.ref[self.key]
+        return rel(x_gpu, self.ref["x_final"]), float(np.max(np.abs(np.asarray(resid_gpu) - r)) / r[0])
+
+    def check(self, parity_log, k, x_gpu, resid_gpu, rerun=None, solver="ba", case="", b_kind="un",
+              dot_mode=0, **info):
+        """Logs the case and asserts the GPU result is within tolerance:
+        1e-4, or 3 d_k for a listed exception.  ``rerun(**opts)`` -> (x,
+        resid) reruns the GPU solve with other options; it is called when an
+        error exceeds 1e-4 (for the record, and for an exception's variant
+        that must meet 1e-4)."""
+        exc = EXCEPTIONS.get((solver, case, b_kind, k, dot_mode))
+        tol_x = self.sens_x if exc else SOLVE_TOL
+        tol_r = self.sens_r if exc else SOLVE_TOL
+        err_img, err_res = self.errors(x_gpu, resid_gpu)
+        variants = {}
+        if rerun is not None and max(err_img, err_res) > SOLVE_TOL:
+            for name, opts in (("dot_mode=1", dict(dot_mode=1)), ("reorth=1", dict(reorth=1))):
+                e = self.errors(*rerun(**opts))
+                variants[name] = {"err_img": e[0], "err_res": e[1]}
+        parity_log(k=k, d_img=self.d_img, d_res=self.d_res, tol_x=tol_x, tol_r=tol_r, err_img=err_img,
+                   err_res=err_res, variants=variants, exception=bool(exc), solver=solver, case=case,
+                   b_kind=b_kind, dot_mode=dot_mode, **info)
+        assert err_res <= tol_r, ("residual history", err_res, tol_r)
+        assert err_img <= tol_x, ("image", err_img, tol_x)
+        if exc and exc["flat_with"] and max(err_img, err_res) > SOLVE_TOL:
+            v = variants[exc["flat_with"]]
+            assert v["err_img"] <= SOLVE_TOL and v["err_res"] <= SOLVE_TOL, (exc["flat_with"], v)
+
+
 def oracle_with_sensitivity(solver, spec, b_kind, b, k, **kw):
     """FP64 oracle solve, plus the tolerances that an FP32-class operator
     error allows at iteration k (image, residual history)."""
@@ -70,7 +136,7 @@ def oracle_with_sensitivity(solver, spec, b_kind, b, k, **kw):
     d_img = rel(pert["x_final"], ref["x_final"])
     key = "data_resid" if kw.get("record_data_resid") else "resid"
     d_res = np.max(np.abs(pert[key] - ref[key])) / ref[key][0]
-    return ref, max(SOLVE_TOL, 3 * d_img), max(SOLVE_TOL, 3 * d_res)
+    return Sensitive(ref, d_img, d_res, key)
 
 
 def data_for(spec, noise=0.01, seed=81):
@@ -87,48 +153,56 @@ CASES = [(ci.CONE_SMALL, "un", 20), (ci.CONE_SMALL, "fbp", 12), (ci.CONE_ANISO, 
 
 @pytest.mark.parametrize("spec,b_kind,k", CASES, ids=lambda v: getattr(v, "name", str(v)))
 @pytest.mark.parametrize("dot_mode", [1, 0])
-def test_bagmres_matches_oracle(ct, spec, b_kind, k, dot_mode):
+def test_bagmres_matches_oracle(ct, parity_log, spec, b_kind, k, dot_mode):
     b, _ = data_for(spec)
     g = ct.Geometry.from_spec(spec)
     x, res = ct.bagmres(g, dev(b), k, b_kind=b_kind, dot_mode=dot_mode)
-    ref, tol_x, tol_r = oracle_with_sensitivity(krylov.ba_gmres, spec, b_kind, b, k, keep_basis=False)
+    sens = oracle_with_sensitivity(krylov.ba_gmres, spec, b_kind, b, k, keep_basis=False)
     assert res.iters == k
-    assert np.max(np.abs(res.resid - ref["resid"])) <= tol_r * ref["resid"][0]
-    assert rel(host(x), ref["x_final"]) <= tol_x, (rel(host(x), ref["x_final"]), tol_x)
     assert np.all(np.diff(res.resid) <= 1e-6 * res.resid[0])
+
+    def rerun(**o):
+        o.setdefault("dot_mode", dot_mode)
+        xx, rr = ct.bagmres(g, dev(b), k, b_kind=b_kind, **o)
+        return host(xx), rr.resid
+    sens.check(parity_log, k, host(x), res.resid, rerun, solver="ba", case=spec.name, b_kind=b_kind,
+               dot_mode=dot_mode)
 
 
 @pytest.mark.parametrize("spec,b_kind,k", [(ci.CONE_SMALL, "un", 12), (ci.PAR2D_64, "un", 20),
                                            (ci.CONE_ANISO, "fbp", 8)],
                          ids=lambda v: getattr(v, "name", str(v)))
-def test_abgmres_matches_oracle(ct, spec, b_kind, k):
+def test_abgmres_matches_oracle(ct, parity_log, spec, b_kind, k):
     b, _ = data_for(spec)
     g = ct.Geometry.from_spec(spec)
     x, res = ct.abgmres(g, dev(b), k, b_kind=b_kind)
-    ref, tol_x, tol_r = oracle_with_sensitivity(krylov.ab_gmres, spec, b_kind, b, k, keep_basis=False)
-    assert np.max(np.abs(res.resid - ref["resid"])) <= tol_r * ref["resid"][0]
-    assert rel(host(x), ref["x_final"]) <= tol_x, (rel(host(x), ref["x_final"]), tol_x)
+    sens = oracle_with_sensitivity(krylov.ab_gmres, spec, b_kind, b, k, keep_basis=False)
+
+    def rerun(**o):
+        xx, rr = ct.abgmres(g, dev(b), k, b_kind=b_kind, **o)
+        return host(xx), rr.resid
+    sens.check(parity_log, k, host(x), res.resid, rerun, solver="ab", case=spec.name, b_kind=b_kind)
 
 
 @pytest.mark.parametrize("spec,b_kind,k", [(ci.PAR2D_64, "un", 30), (ci.CONE_SMALL, "at", 15),
                                            (ci.CONE_SMALL, "un", 8)],
                          ids=lambda v: getattr(v, "name", str(v)))
-def test_cgls_matches_oracle(ct, spec, b_kind, k):
+def test_cgls_matches_oracle(ct, parity_log, spec, b_kind, k):
     b, _ = data_for(spec)
     g = ct.Geometry.from_spec(spec)
     x, res = ct.cgls(g, dev(b), k, b_kind=b_kind)
-    ref, tol_x, tol_r = oracle_with_sensitivity(krylov.cgls, spec, b_kind, b, k)
-    assert np.max(np.abs(res.resid - ref["resid"])) <= tol_r * ref["resid"][0]
-    assert rel(host(x), ref["x_final"]) <= tol_x, (rel(host(x), ref["x_final"]), tol_x)
+    sens = oracle_with_sensitivity(krylov.cgls, spec, b_kind, b, k)
+    sens.check(parity_log, k, host(x), res.resid, solver="cgls", case=spec.name, b_kind=b_kind)
 
 
-def test_cgls_record_data_resid(ct):
+def test_cgls_record_data_resid(ct, parity_log):
     spec = ci.CONE_SMALL
     b, _ = data_for(spec)
     g = ct.Geometry.from_spec(spec)
     x, res = ct.cgls(g, dev(b), 6, b_kind="un", record_data_resid=True)
-    ref, _, tol_r = oracle_with_sensitivity(krylov.cgls, spec, "un", b, 6, record_data_resid=True)
-    assert np.max(np.abs(res.resid - ref["data_resid"])) <= tol_r * ref["data_resid"][0]
+    sens = oracle_with_sensitivity(krylov.cgls, spec, "un", b, 6, record_data_resid=True)
+    sens.check(parity_log, 6, host(x), res.resid, solver="cgls", case=spec.name, b_kind="un",
+               record_data_resid=True)
 
 
 def test_unmatched_cgls_diverges_on_gpu(ct):
@@ -218,14 +292,13 @@ def test_host_buffer_solve_equals_device_solve(ct):
         ct.ct_bagmres_solve_host(g, dev(b), 8, xh)
 
 
-def test_reorthogonalisation_keeps_parity(ct):
+def test_reorthogonalisation_keeps_parity(ct, parity_log):
     spec = ci.CONE_SMALL
     b, _ = data_for(spec)
     g = ct.Geometry.from_spec(spec)
     x, res = ct.bagmres(g, dev(b), 20, reorth=1)
-    ref, tol_x, tol_r = oracle_with_sensitivity(krylov.ba_gmres, spec, "un", b, 20, keep_basis=False)
-    assert rel(host(x), ref["x_final"]) <= tol_x
-    assert np.max(np.abs(res.resid - ref["resid"])) <= tol_r * ref["resid"][0]
+    sens = oracle_with_sensitivity(krylov.ba_gmres, spec, "un", b, 20, keep_basis=False)
+    sens.check(parity_log, 20, host(x), res.resid, solver="ba", case=spec.name, b_kind="un", reorth=1)
 
 
 @pytest.mark.parametrize("dot_mode", [0, 1])
@@ -293,12 +366,11 @@ def test_full_size_256_bagmres_properties(ct, b_kind, k):
     assert abs(r1 - r[1]) <= 1e-4 * r[0], (r1, r[1])
 
 
-def test_error_history_matches_oracle(ct):
+def test_error_history_matches_oracle(ct, parity_log):
     """ct_bagmres_solve_err: err[j] = ||x_j - x_true|| of every iterate (the
     semi-convergence curve, Sec. III Fig. 4) against the FP64 oracle's
-    iterates, each within max(1e-4 ||x_j||, 3 d_j), d_j the distance between
-    the oracle's iterate and its own run with FP32-class (1e-6) operator
-    error; x_out is the plain solve's x_k."""
+    iterates, each within 1e-4 ||x_j|| (the image bar); x_out is the plain
+    solve's x_k."""
     spec, k = ci.CONE_SMALL, 12
     b, x_true = data_for(spec)
     g = ct.Geometry.from_spec(spec)
@@ -314,10 +386,15 @@ def test_error_history_matches_oracle(ct):
     pert = krylov.ba_gmres(_perturbed(ops.A, rng), _perturbed(ops.B, rng), b64, k, keep_basis=False)
     xt = x_true.reshape(-1)
     assert abs(err[0] - np.linalg.norm(xt)) <= 1e-5 * np.linalg.norm(xt)
+    worst = 0.0
     for j in range(1, k + 1):
         xj = ref["x"][j - 1]
-        tol = max(SOLVE_TOL * np.linalg.norm(xj), 3 * np.linalg.norm(pert["x"][j - 1] - xj))
-        assert abs(err[j] - np.linalg.norm(xj - xt)) <= tol, (j, err[j], np.linalg.norm(xj - xt), tol)
+        assert abs(err[j] - np.linalg.norm(xj - xt)) <= SOLVE_TOL * np.linalg.norm(xj), \
+            (j, err[j], np.linalg.norm(xj - xt))
+        worst = max(worst, abs(err[j] - np.linalg.norm(xj - xt)) / np.linalg.norm(xj))
+    d = max(np.linalg.norm(pert["x"][j - 1] - ref["x"][j - 1]) / np.linalg.norm(ref["x"][j - 1])
+            for j in range(1, k + 1))
+    parity_log(k=k, d_img=d, err_img=worst, tol_x=SOLVE_TOL, solver="ba_err_hist", case=spec.name, b_kind="fbp")
 
 
 def test_error_history_marks_iterations_not_done(ct):
@@ -332,7 +409,7 @@ def test_error_history_marks_iterations_not_done(ct):
 
 @pytest.mark.parametrize("spec,b_kind", [(ci.CONE_SMALL, "un"), (ci.PAR2D_64, "fbp")],
                          ids=lambda v: getattr(v, "name", str(v)))
-def test_restarted_matches_oracle(ct, spec, b_kind):
+def test_restarted_matches_oracle(ct, parity_log, spec, b_kind):
     """ct_bagmres_restarted, 3 cycles of GMRES(5), against the FP64 oracle's
     restarted solve (same tolerance rule as the unrestarted solves)."""
     m, cycles = 5, 3
@@ -340,12 +417,12 @@ def test_restarted_matches_oracle(ct, spec, b_kind):
     g = ct.Geometry.from_spec(spec)
     x = torch.empty(spec.vol_shape, device="cuda")
     res = ct.ct_bagmres_restarted(g, dev(b), m, cycles, x, ct.make_opts(b_kind=b_kind))
-    ref, tol_x, tol_r = oracle_with_sensitivity(
+    sens = oracle_with_sensitivity(
         lambda A, B, bb, k: krylov.ba_gmres_restarted(A, B, bb, m, cycles), spec, b_kind, b, m * cycles)
     assert res.iters == m * cycles
-    assert np.max(np.abs(res.resid - ref["resid"])) <= tol_r * ref["resid"][0]
-    assert rel(host(x), ref["x_final"]) <= tol_x, (rel(host(x), ref["x_final"]), tol_x)
     assert np.all(np.diff(res.resid) <= 1e-6 * res.resid[0])
+    sens.check(parity_log, m * cycles, host(x), res.resid, solver="ba_restarted", case=spec.name,
+               b_kind=b_kind)
 
 
 def test_restarted_single_cycle_equals_solve(ct):
@@ -363,7 +440,7 @@ def test_restarted_single_cycle_equals_solve(ct):
 
 @pytest.mark.parametrize("spec,b_kind,k", [(ci.CONE_SMALL, "un", 12), (ci.PAR2D_64, "fbp", 15)],
                          ids=lambda v: getattr(v, "name", str(v)))
-def test_bagmres_with_siddon_projector_matches_oracle(ct, spec, b_kind, k):
+def test_bagmres_with_siddon_projector_matches_oracle(ct, parity_log, spec, b_kind, k):
     """BA-GMRES with the line-intersection A and the same unmatched B."""
     b, _ = data_for(spec)
     g = ct.Geometry.from_spec(spec, projector="siddon")
@@ -374,7 +451,11 @@ def test_bagmres_with_siddon_projector_matches_oracle(ct, spec, b_kind, k):
     ref = krylov.ba_gmres(ops.A, ops.B, b64, k, keep_basis=False)
     rng = np.random.default_rng(97)
     pert = krylov.ba_gmres(_perturbed(ops.A, rng), _perturbed(ops.B, rng), b64, k, keep_basis=False)
-    tol_x = max(SOLVE_TOL, 3 * rel(pert["x_final"], ref["x_final"]))
-    tol_r = max(SOLVE_TOL, 3 * np.max(np.abs(pert["resid"] - ref["resid"])) / ref["resid"][0])
-    assert np.max(np.abs(res.resid - ref["resid"])) <= tol_r * ref["resid"][0]
-    assert rel(host(x), ref["x_final"]) <= tol_x, (rel(host(x), ref["x_final"]), tol_x)
+    sens = Sensitive(ref, rel(pert["x_final"], ref["x_final"]),
+                     np.max(np.abs(pert["resid"] - ref["resid"])) / ref["resid"][0])
+
+    def rerun(**o):
+        xx = torch.empty(spec.vol_shape, device="cuda")
+        rr = ct.ct_bagmres_solve(g, dev(b), k, xx, ct.make_opts(b_kind=b_kind, **o))
+        return host(xx), rr.resid
+    sens.check(parity_log, k, host(x), res.resid, rerun, solver="ba_siddon", case=spec.name, b_kind=b_kind)
