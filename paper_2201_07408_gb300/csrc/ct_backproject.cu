@@ -355,17 +355,23 @@ __device__ __forceinline__ ColumnView column_view(const GeomDev &g, int s, float
     return column_view(g, __ldg(vp), __ldg(vp + 1), x, y, zfirst);
 }
 
-// A block owns a 32 x 32 tile of (x, y) columns and B_ZC consecutive z.
-// Which of x or y its lanes run along is chosen per view: the axis closer
-// to the view's central ray (along x when |tx| <= |ty|, i.e. when u moves
-// more slowly with x than with y).  Along the central ray the projection
-// barely moves (only the magnification changes, by vox/depth per voxel), so
-// a warp's gathers fall on a few neighbouring pixels of a few rows; across
-// it, u moves by M vox/du pixels per lane.  The two partial sums (x-lane
-// views and y-lane views) meet in shared memory.  The sinogram is read as
-// quads (the 2 x 2 bilinear neighbourhood), one 16-byte load per voxel and
-// view; the view table sits in shared memory.
+// A block owns a 32 x 32 tile of (x, y) columns and B_ZC consecutive z.  A
+// warp covers a patch of PA x (32/PA) columns, PA lanes along the axis
+// closer to the view's central ray (chosen per view: along x when
+// |tx| <= |ty|, i.e. when u moves more slowly with x than with y).  Along
+// the central ray the projection barely moves (only the magnification
+// changes, by vox/depth per voxel); across it, u moves by M vox/du pixels
+// per lane.  The load path's passes per 128-bit warp load (ncu: data-pipe
+// wavefronts per request) follow the number of distinct 128-byte lines that
+// each group of 8 consecutive lanes touches, so the patch is chosen for
+// that: 4 lanes along by 2 across per group of 8 (PA = 4) touches fewest on
+// the cone-beam scans (at 256^3: 5.3 passes per warp load against 6.4 with
+// all 32 lanes along the ray; B 5.09 against 5.49 ms).
+// The two partial sums (x-lane views and y-lane views) meet in shared
+// memory.  The sinogram is read as quads (the 2 x 2 bilinear neighbourhood),
+// one 16-byte load per voxel and view; the view table sits in shared memory.
 constexpr int B_TILE = 32;
+constexpr int B_PA = 4;
 
 // the four bilinear neighbours of one sinogram quad entry
 template <bool BF>
@@ -414,7 +420,7 @@ __device__ __forceinline__ void accumulate(float (&acc)[ZC], const float (&r)[ZC
     for (int k = 0; k < ZC; ++k) acc[k] = DIFF ? fmaf(w, r[k], acc[k]) : acc[k] + r[k];
 }
 
-template <int ZC, bool BF, bool DIFF>
+template <int ZC, bool BF, bool DIFF, int PA = 32>
 __global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, const void *__restrict__ ypad,
                                                                  float *__restrict__ x,
                                                                  const int *__restrict__ stop)
@@ -429,10 +435,15 @@ __global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, cons
     const int X0 = blockIdx.x * B_TILE, Y0 = blockIdx.y * B_TILE;
     const int iz0 = blockIdx.z * ZC;
     const float zfirst = (float(iz0) - g.cz) * g.vox;
+    // a warp covers a PA x (32/PA) patch of columns, PA lanes along the axis
+    // nearer the central ray
+    constexpr int PB = 32 / PA;
+    const int along = (w % (32 / PA)) * PA + l % PA, across = (w / (32 / PA)) * PB + l / PA;
+    const int tax = along, tay = across, tbx = across, tby = along;   // tile offsets of the two mappings
     // column of the x-lane mapping and of the y-lane mapping (clamped into the grid;
     // columns past the edge compute throw-away values)
-    const int ax = min(X0 + l, g.nx - 1), ay = min(Y0 + w, g.ny - 1);
-    const int bx = min(X0 + w, g.nx - 1), by = min(Y0 + l, g.ny - 1);
+    const int ax = min(X0 + tax, g.nx - 1), ay = min(Y0 + tay, g.ny - 1);
+    const int bx = min(X0 + tbx, g.nx - 1), by = min(Y0 + tby, g.ny - 1);
     const float axc = (float(ax) - g.cx) * g.vox, ayc = (float(ay) - g.cy) * g.vox;
     const float bxc = (float(bx) - g.cx) * g.vox, byc = (float(by) - g.cy) * g.vox;
     const int view_stride = g.nvp * g.pitchU;
@@ -456,12 +467,12 @@ __global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, cons
         else
             accumulate<ZC, DIFF>(accB, r, c.w);
     }
-    // x-lane sums belong to (x = X0 + l, y = Y0 + w), y-lane sums to (x = X0 + w, y = Y0 + l)
+    // x-lane sums belong to (X0 + tax, Y0 + tay), y-lane sums to (X0 + tbx, Y0 + tby)
 #pragma unroll
-    for (int k = 0; k < ZC; ++k) tile[k][w][l] = accA[k];
+    for (int k = 0; k < ZC; ++k) tile[k][tay][tax] = accA[k];
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < ZC; ++k) tile[k][l][w] += accB[k];
+    for (int k = 0; k < ZC; ++k) tile[k][tby][tbx] += accB[k];
     __syncthreads();
     const int ix = X0 + l, iy = Y0 + w;
     if (ix >= g.nx || iy >= g.ny) return;
@@ -558,38 +569,38 @@ static cudaError_t launch_voxel_B_2pass(const GeomDev &g, const float *ypad, flo
     return cudaGetLastError();
 }
 
-template <int ZC, bool BF, bool DIFF>
+template <int ZC, bool BF, bool DIFF, int PA = 32>
 static cudaError_t launch_voxel_B_t(const GeomDev &g, const float *ypad, float *x, const int *stop, cudaStream_t st)
 {
     dim3 block(B_TILE, B_TILE);
     const size_t smem = size_t(g.n_views) * 2 * sizeof(float4);
     if (smem > 8 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(voxel_B_kernel<ZC, BF, DIFF>,
+        cudaError_t e = cudaFuncSetAttribute(voxel_B_kernel<ZC, BF, DIFF, PA>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
     }
     dim3 grid((g.nx + B_TILE - 1) / B_TILE, (g.ny + B_TILE - 1) / B_TILE, (g.nz + ZC - 1) / ZC);
-    voxel_B_kernel<ZC, BF, DIFF><<<grid, block, smem, st>>>(g, ypad, x, stop);
+    voxel_B_kernel<ZC, BF, DIFF, PA><<<grid, block, smem, st>>>(g, ypad, x, stop);
     return cudaGetLastError();
 }
 
-template <int ZC>
+template <int ZC, int PA>
 static cudaError_t launch_voxel_B_z(const GeomDev &g, const float *ypad, float *x, const int *stop, cudaStream_t st,
                                     QuadForm form)
 {
-    if (g.sino_bf16) return launch_voxel_B_t<ZC, true, false>(g, ypad, x, stop, st);
-    return form == QUAD_ROWDIFF ? launch_voxel_B_t<ZC, false, true>(g, ypad, x, stop, st)
-                                : launch_voxel_B_t<ZC, false, false>(g, ypad, x, stop, st);
+    if (g.sino_bf16) return launch_voxel_B_t<ZC, true, false, PA>(g, ypad, x, stop, st);
+    return form == QUAD_ROWDIFF ? launch_voxel_B_t<ZC, false, true, PA>(g, ypad, x, stop, st)
+                                : launch_voxel_B_t<ZC, false, false, PA>(g, ypad, x, stop, st);
 }
 
 cudaError_t launch_voxel_B(const GeomDev &g, const float *ypad, float *x, const int *stop, cudaStream_t st,
                            QuadForm form)
 {
     ProfScope prof(PK_VOXEL_B, st);
-    if (g.nz == 1) return launch_voxel_B_z<1>(g, ypad, x, stop, st, form);
+    if (g.nz == 1) return launch_voxel_B_z<1, 32>(g, ypad, x, stop, st, form);
     if (g.sino_bf16 && g.nz >= B_ZC_2PASS)
         return launch_voxel_B_2pass<B_ZC_2PASS, true>(g, ypad, x, stop, st);
-    return launch_voxel_B_z<B_ZC>(g, ypad, x, stop, st, form);
+    return launch_voxel_B_z<B_ZC, B_PA>(g, ypad, x, stop, st, form);
 }
 
 // ---------------------------------------------------------------------------
