@@ -218,14 +218,10 @@ def aggregate_over_ranks(elapsed_s, iters, world, device=None):
 NCU_TRAFFIC = {
     # (kernel, storage, workload): (bytes per launch, source file,
     # sha256 of that file followed by ct_internal.cuh at capture time)
-    ("voxel_B", "f32", "cone_256"): (1415970560 + 68444672, "ct_backproject.cu",
-                                     "3c04c3c123042c2d27467272b5fc00877bcbe9308090dcd35220e8f45ef0d1bf"),
-    ("voxel_B", "bf16", "cone_256"): (565138944 + 61659392, "ct_backproject.cu",
-                                      "3c04c3c123042c2d27467272b5fc00877bcbe9308090dcd35220e8f45ef0d1bf"),
-    ("joseph_A", "f32", "cone_256"): (410601984 + 137186816, "ct_project.cu",
-                                      "f3d9d23f1a744617c05e296b8a7e307903d3f87e900863f50edce8770f2a3acc"),
-    ("joseph_A", "bf16", "cone_256"): (429411840 + 153559040, "ct_project.cu",
-                                       "f3d9d23f1a744617c05e296b8a7e307903d3f87e900863f50edce8770f2a3acc"),
+    ("voxel_B", "f32", "cone_256"): (1415469000 + 68405504, "ct_backproject.cu",
+                                     "5af7276986cfcebb938b5d180d4e8b0eca3afc56389e16b1ff2614291a11a982"),
+    ("joseph_A", "f32", "cone_256"): (412170240 + 137536512, "ct_project.cu",
+                                      "bb34b7769afe39007cc6cd797646a5466885e472cdc48f6d276a16769987c6e1"),
 }
 
 

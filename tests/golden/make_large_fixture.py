@@ -15,6 +15,10 @@ Cases (one file ``oracle_<case>.npz`` each, beside this script):
   of 0.75 mm) with Poisson data, counts ~ Poisson(1e5 exp(-A x_true)),
   b = -log(counts/1e5), and BA-GMRES with B = B_FBP (Sec. III), 40
   iterations.
+* ``c4_vjp``: the gradient through a converged BA-GMRES solve on the 128^3
+  scan (B = B_un): dL/db = B^T z with (A^T B^T) z = g_x, z from 40 GMRES
+  iterations on A^T B^T, for a seeded smooth g_x (the "data" here is g_x,
+  an image-space vector; the stored sample is of dL/db).
 
 Each case runs the solver twice: once as it is, once with every operator
 output multiplied by (1 + 1e-6 N(0,1)) (seeded), the relative error class
@@ -25,12 +29,12 @@ FP32 implementation can be expected to reach.
 Stored per case: the geometry, k, the data's norm and a seeded sample of
 its entries (so a test that regenerates b can check it has the same data),
 the residual history of both runs (and the data residual for CGLS), the
-final iterate's norm, the final iterate at a seeded sample of voxels, and
-d_img = ||x_pert - x|| / ||x|| with the residual sensitivity
-d_res = max_j |r_pert[j] - r[j]| / r[0].
+final iterate's norm, the final iterate at a seeded sample of its entries
+(voxels; detector readings for the gradient), and d_img = ||x_pert - x|| /
+||x|| with the residual sensitivity d_res = max_j |r_pert[j] - r[j]| / r[0].
 
 Run from the repository root (the 256^3 case takes hours on 8 cores):
-    python tests/golden/make_large_fixture.py c2_ba c2_ab c2_cgls c3_ba
+    python tests/golden/make_large_fixture.py c2_ba c2_ab c2_cgls c3_ba c4_vjp
 """
 import json
 import os
@@ -59,11 +63,15 @@ CASES = {
     "c2_ab": dict(spec="cone_128", solver="ab", b_kind="un", k=50, data="noiseless"),
     "c2_cgls": dict(spec="cone_128", solver="cgls", b_kind="un", k=50, data="noiseless"),
     "c3_ba": dict(spec="cone_256", solver="ba", b_kind="fbp", k=40, data="poisson"),
+    "c4_vjp": dict(spec="cone_128", solver="vjp", b_kind="un", k=40, data="smooth_gx"),
 }
 
 
 def case_data(spec, kind):
-    """The case's data b (float32, as the GPU receives it) and x_true."""
+    """The case's data b (float32, as the GPU receives it) and x_true; for
+    the gradient case the image-space vector g_x instead of b."""
+    if kind == "smooth_gx":
+        return ci.smooth_volume(spec, seed=3).astype(np.float32), None
     x_true = ci.phantom(spec)[0]
     p = oracle.project_A(spec, x_true.astype(np.float64))
     if kind == "poisson":
@@ -81,6 +89,9 @@ def _perturbed(f, rng):
 
 
 def run_solver(solver, A, B, b64, k):
+    if solver == "vjp":   # A, B are A^T, B^T here
+        out = krylov.ba_gmres_vjp(A, B, b64, k)
+        return dict(resid=np.asarray(out["resid"], dtype=np.float64), x_final=np.asarray(out["gb"]).reshape(-1))
     if solver == "ba":
         out = krylov.ba_gmres(A, B, b64, k, keep_basis=False)
     elif solver == "ab":
@@ -99,16 +110,22 @@ def make(name):
     t0 = time.time()
     b, _ = case_data(spec, c["data"])
     b64 = b.astype(np.float64).reshape(-1)
-    ops = oracle.Operators(spec, c["b_kind"])
-    ref = run_solver(c["solver"], ops.A, ops.B, b64, c["k"])
+    if c["solver"] == "vjp":
+        adj = oracle.AdjointOperators(spec, c["b_kind"])
+        op1, op2 = adj.At, adj.Bt
+    else:
+        ops = oracle.Operators(spec, c["b_kind"])
+        op1, op2 = ops.A, ops.B
+    ref = run_solver(c["solver"], op1, op2, b64, c["k"])
     t1 = time.time()
     rng = np.random.default_rng(PERTURB_SEED)
-    pert = run_solver(c["solver"], _perturbed(ops.A, rng), _perturbed(ops.B, rng), b64, c["k"])
+    pert = run_solver(c["solver"], _perturbed(op1, rng), _perturbed(op2, rng), b64, c["k"])
     t2 = time.time()
     key = "data_resid" if c["solver"] == "cgls" else "resid"
     x = ref["x_final"]
-    vox = ci.sample_indices(spec.n, IMAGE_SAMPLES, seed=IMAGE_SAMPLE_SEED)
-    rays = ci.sample_indices(spec.m, DATA_SAMPLES, seed=DATA_SAMPLE_SEED)
+    # the gradient case's output lives in data space and its input in image space
+    vox = ci.sample_indices(x.size, IMAGE_SAMPLES, seed=IMAGE_SAMPLE_SEED)
+    rays = ci.sample_indices(b64.size, DATA_SAMPLES, seed=DATA_SAMPLE_SEED)
     meta = dict(case=name, spec=spec.as_dict(), solver=c["solver"], b_kind=c["b_kind"], k=c["k"],
                 data=c["data"], op_eps=OP_EPS, perturb_seed=PERTURB_SEED,
                 image_sample_seed=IMAGE_SAMPLE_SEED, data_sample_seed=DATA_SAMPLE_SEED,

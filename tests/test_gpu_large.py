@@ -118,3 +118,27 @@ def test_gmres_matches_stored_oracle_solve(ct, parity_log, name):
     assert res.iters == meta["k"]
     assert np.all(np.diff(res.resid) <= 1e-6 * res.resid[0])
     compare(parity_log, name, meta, d, x, res.resid)
+
+
+def test_cgls_unmatched_matches_stored_oracle_and_its_divergence(ct, parity_log):
+    name = "c2_cgls"
+    meta, d = load_case(name)
+    spec = ci.WORKLOADS[meta["spec"]["name"]]
+    b = regenerate_data(meta, d)
+    g = ct.Geometry.from_spec(spec)
+    x = torch.empty(spec.vol_shape, device="cuda")
+    res = ct.ct_cgls_solve(g, torch.from_numpy(b).cuda(), meta["k"], x,
+                           ct.make_opts(b_kind=meta["b_kind"], record_data_resid=True))
+    assert res.iters == meta["k"]
+    compare(parity_log, name, meta, d, x, res.resid, key="data_resid")
+    # Sec. III (Fig. 2): with the unmatched pair the data residual of CGLS
+    # reaches a minimum and then grows; the stored oracle solve of this scan
+    # has its minimum at iteration 26 and ends 8.7x above it, and the GPU
+    # must show the same
+    ref = d["data_resid"]
+    r = res.resid[:meta["k"] + 1]
+    j_ref, j_gpu = int(np.argmin(ref)), int(np.argmin(r))
+    parity_log(k=meta["k"], case=name, oracle_min_at=j_ref, gpu_min_at=j_gpu,
+               oracle_final_over_min=float(ref[-1] / ref[j_ref]), gpu_final_over_min=float(r[-1] / r[j_gpu]))
+    assert 0 < j_ref < meta["k"] and ref[-1] > 2 * ref[j_ref]
+    assert j_gpu == j_ref and r[-1] > 2 * r[j_gpu]
