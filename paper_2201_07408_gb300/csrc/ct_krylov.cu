@@ -762,15 +762,109 @@ static size_t gmres_bytes(const GeomDev &g, int k, bool ab, int b_kind, bool ext
     return ar.used;
 }
 
+// Host-resident basis streamed through the device by the copy engine.  The
+// basis vectors live in page-locked host memory; the newest one is written to
+// a device buffer (vnew) and copied out on a copy stream while the operators
+// run; each MGS sweep brings the older vectors back into a ring of three
+// device buffers, V_i into slot i mod 3, two vectors ahead of the pass that
+// reads them (the copy of V_{i+2} waits for pass i, the last reader of the
+// slot's previous vector).  The kernels read only device memory, so a pass
+// runs at the copy's pace instead of at the kernels' own reads over the
+// host link.
+struct Stager {
+    cudaStream_t cs = nullptr;       // copy stream
+    void *ring[3] = {};              // device slots, one basis vector each
+    void *vnew = nullptr;            // device copy of the newest vector
+    char *host = nullptr;            // host basis, vector i at host + i * vbytes_ld
+    size_t vbytes = 0;               // bytes copied per vector
+    size_t vbytes_ld = 0;            // stride of the host vectors
+    cudaEvent_t ev[8] = {};
+    int evi = 0;
+    cudaEvent_t vnew_free = nullptr; // the last copy out of vnew has finished
+    cudaEvent_t ready[3] = {};       // per slot: its current vector has arrived
+
+    cudaEvent_t next_event() { cudaEvent_t e = ev[evi]; evi = (evi + 1) % 8; return e; }
+    // copies host vector i into slot i mod 3 after the work enqueued on s so far
+    cudaError_t fetch(int i, cudaStream_t s)
+    {
+        cudaEvent_t e = next_event();
+        cudaError_t r = cudaEventRecord(e, s);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(cs, e, 0);
+        if (r == cudaSuccess)
+            r = cudaMemcpyAsync(ring[i % 3], host + size_t(i) * vbytes_ld, vbytes, cudaMemcpyHostToDevice, cs);
+        if (r == cudaSuccess) r = cudaEventRecord(ready[i % 3], cs);
+        return r;
+    }
+    // the device copy of V_i for a sweep whose newest vector is V_j (in vnew);
+    // makes s wait for its arrival
+    const void *vector(int i, int j, cudaStream_t s)
+    {
+        if (i == j) return vnew;
+        cudaStreamWaitEvent(s, ready[i % 3], 0);
+        return ring[i % 3];
+    }
+    // copies vnew out to host vector j after the work enqueued on s so far
+    cudaError_t store_new(int j, cudaStream_t s)
+    {
+        cudaEvent_t e = next_event();
+        cudaError_t r = cudaEventRecord(e, s);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(cs, e, 0);
+        if (r == cudaSuccess)
+            r = cudaMemcpyAsync(host + size_t(j) * vbytes_ld, vnew, vbytes, cudaMemcpyDeviceToHost, cs);
+        if (r == cudaSuccess) r = cudaEventRecord(vnew_free, cs);
+        return r;
+    }
+};
+
+// One MGS sweep (passes i = 0..j+1) over a staged basis: V_i for i < j comes
+// through the ring, V_j from vnew.
+// With `prefetched`, V_0 and V_1 were fetched already (at the start of the
+// iteration, so that their copies overlap the operators).
+static cudaError_t staged_sweep(Stager &sg, int mode, bool vbf16, float *q, int j, double *hcol, size_t len,
+                                double *partials, unsigned *ctr, double *first_ss, double *last_ss,
+                                const int *stop, const int *skip, cudaStream_t s, bool prefetched)
+{
+    cudaError_t e = cudaSuccess;
+    if (!prefetched && 0 < j) e = sg.fetch(0, s);
+    if (!prefetched && e == cudaSuccess && 1 < j) e = sg.fetch(1, s);
+    for (int i = 0; i <= j + 1 && e == cudaSuccess; ++i) {
+        const void *vprev = i > 0 ? sg.vector(i - 1, j, s) : nullptr;
+        const void *vcur = i <= j ? sg.vector(i, j, s) : nullptr;
+        const double *hprev = i > 0 ? hcol + (i - 1) : nullptr;
+        double *odot = i <= j ? hcol + i : nullptr;
+        double *oss = i == 0 ? first_ss : (i == j + 1 ? last_ss : nullptr);
+        e = mgs_pass_typed(mode, vbf16, q, vprev, hprev, vcur, len, partials, ctr, odot, oss, stop, skip, s);
+        // slot (i + 2) mod 3 held V_{i-1}, whose last reader was this pass
+        if (e == cudaSuccess && i + 2 < j) e = sg.fetch(i + 2, s);
+    }
+    return e;
+}
+
 // Enqueues the MGS sweep of iteration j (the new vector q against
 // V_0..V_j) and its Givens step.
 static cudaError_t arnoldi_orthogonalise(GmresWs &w, float *q, int j, int k, size_t len, const ct_solve_opts &o,
-                                         cudaStream_t s)
+                                         cudaStream_t s, Stager *sg = nullptr)
 {
     const int *stop = &w.st->status;
     unsigned *ctr = &w.st->counter;
     double *hcol = w.H + size_t(j) * (k + 1);
     cudaError_t e = fault_poison(q, j + 1, stop, s);
+    if (sg) {
+        if (e == cudaSuccess)
+            e = staged_sweep(*sg, o.dot_mode, w.vbf16, q, j, hcol, len, w.partials, ctr, &w.st->ref_sumsq,
+                             &w.st->sumsq, stop, nullptr, s, true);
+        if (e != cudaSuccess) return e;
+        const double *H2s = nullptr;
+        if (o.reorth) {
+            { ProfScope prof(PK_SMALL, s); reorth_decide_kernel<<<1, 1, 0, s>>>(w.st); }
+            e = staged_sweep(*sg, o.dot_mode, w.vbf16, q, j, w.H2, len, w.partials, ctr, nullptr, &w.st->sumsq,
+                             stop, &w.st->reorth_skip, s, false);
+            if (e != cudaSuccess) return e;
+            H2s = w.H2;
+        }
+        { ProfScope prof(PK_SMALL, s); givens_kernel<<<1, 1, 0, s>>>(j, k, w.H, H2s, w.R, w.cs, w.sn, w.g, w.resid, w.st, o.tol); }
+        return cudaGetLastError();
+    }
     for (int i = 0; i <= j + 1 && e == cudaSuccess; ++i) {
         const void *vprev = i > 0 ? w.vec(i - 1) : nullptr;
         const double *hprev = i > 0 ? hcol + (i - 1) : nullptr;
@@ -851,12 +945,22 @@ static cudaError_t ba_start(const GeomDev &g, GmresWs &w, const float *b, int km
 // Iteration j (0-based): v_j = q / ||q|| joins the basis, q = B A v_j is
 // orthogonalised against v_0..v_j, and the Givens step updates the residual.
 static cudaError_t ba_iteration(const GeomDev &g, GmresWs &w, int j, int kmax, size_t n, const ct_solve_opts &o,
-                                cudaStream_t s)
+                                cudaStream_t s, Stager *sg = nullptr)
 {
     NvtxRange iter_range("BA-GMRES iteration");
     const int *stop = &w.st->status;
+    cudaError_t e = cudaSuccess;
+    // a staged basis: vnew is rewritten only after its previous copy out; the
+    // first two vectors of this iteration's sweep start coming in now
+    if (sg) {
+        e = cudaStreamWaitEvent(s, sg->vnew_free, 0);
+        if (e == cudaSuccess && 0 < j) e = sg->fetch(0, s);
+        if (e == cudaSuccess && 1 < j) e = sg->fetch(1, s);
+    }
     // v_j = q / ||q|| stored in the basis while the projector's plane copies are built
-    cudaError_t e = launch_plane_copies(g, w.q, &w.st->inv_norm, w.vec(j), w.ob.Xc, w.ob.Yc, stop, s);
+    if (e == cudaSuccess)
+        e = launch_plane_copies(g, w.q, &w.st->inv_norm, sg ? sg->vnew : w.vec(j), w.ob.Xc, w.ob.Yc, stop, s);
+    if (e == cudaSuccess && sg) e = sg->store_new(j, s);
     if (e != cudaSuccess) return e;
     // q = B A v_j
     if (o.b_kind == CT_B_UN) {
@@ -866,7 +970,7 @@ static cudaError_t ba_iteration(const GeomDev &g, GmresWs &w, int j, int kmax, s
         e = launch_project_A(g, w.ob.Xc, w.ob.Yc, w.ob.t, plain_layout(g), stop, s);
         if (e == cudaSuccess) e = apply_B(g, o.b_kind, w.ob.t, nullptr, false, w.ob, w.q, stop, s, nullptr);
     }
-    if (e == cudaSuccess) e = arnoldi_orthogonalise(w, w.q, j, kmax, n, o, s);
+    if (e == cudaSuccess) e = arnoldi_orthogonalise(w, w.q, j, kmax, n, o, s, sg);
     return e;
 }
 
@@ -1314,6 +1418,8 @@ struct ct_gmres_state {
     int basis = CT_BASIS_DEVICE;
     void *dev_mem = nullptr;      // cudaMalloc'ed workspace (all but a host basis)
     void *host_basis = nullptr;   // cudaHostAlloc'ed basis (CT_BASIS_HOST)
+    void *stage_mem = nullptr;    // cudaMalloc'ed ring and newest-vector buffers (CT_BASIS_HOST)
+    ct::Stager stager;            // streams a host basis through stage_mem (CT_BASIS_HOST)
     ct::GmresWs w;
     int started = 0;
     int k_done = 0;               // iterations done, as of the last synchronising call
@@ -1325,9 +1431,84 @@ namespace ct {
 static void state_free(ct_gmres_state *st)
 {
     if (!st) return;
+    Stager &sg = st->stager;
+    if (sg.cs) cudaStreamSynchronize(sg.cs);
+    for (cudaEvent_t e : sg.ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : sg.ready)
+        if (e) cudaEventDestroy(e);
+    if (sg.vnew_free) cudaEventDestroy(sg.vnew_free);
+    if (sg.cs) cudaStreamDestroy(sg.cs);
     if (st->dev_mem) cudaFree(st->dev_mem);
+    if (st->stage_mem) cudaFree(st->stage_mem);
     if (st->host_basis) cudaFreeHost(st->host_basis);
     delete st;
+}
+
+// The copy stream, events and device buffers of a staged host basis.
+static cudaError_t stager_init(ct_gmres_state *st)
+{
+    Stager &sg = st->stager;
+    const GmresWs &w = st->w;
+    const size_t esz = w.vbf16 ? 2 : 4;
+    sg.vbytes = st->geom->n * esz;
+    sg.vbytes_ld = w.ldv * esz;
+    const size_t slot = Arena::align(sg.vbytes);
+    cudaError_t e = cudaMalloc(&st->stage_mem, 4 * slot);
+    if (e != cudaSuccess) return e;
+    char *base = static_cast<char *>(st->stage_mem);
+    for (int i = 0; i < 3; ++i) sg.ring[i] = base + i * slot;
+    sg.vnew = base + 3 * slot;
+    sg.host = static_cast<char *>(st->host_basis);
+    e = cudaStreamCreateWithFlags(&sg.cs, cudaStreamNonBlocking);
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&sg.ev[i], cudaEventDisableTiming);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&sg.ready[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sg.vnew_free, cudaEventDisableTiming);
+    return e;
+}
+
+__global__ void __launch_bounds__(RED_BLOCK) basis_axpy_kernel_f32(float *__restrict__ x, const float *__restrict__ v,
+                                                                   const double *__restrict__ y, int i, size_t len)
+{
+    const float yi = float(y[i]);
+    for (size_t e = blockIdx.x * size_t(RED_BLOCK) + threadIdx.x; e < len; e += size_t(gridDim.x) * RED_BLOCK)
+        x[e] = fmaf(yi, v[e], i == 0 ? 0.0f : x[e]);
+}
+
+__global__ void __launch_bounds__(RED_BLOCK) basis_axpy_kernel_bf16(float *__restrict__ x,
+                                                                    const __nv_bfloat16 *__restrict__ v,
+                                                                    const double *__restrict__ y, int i, size_t len)
+{
+    const float yi = float(y[i]);
+    for (size_t e = blockIdx.x * size_t(RED_BLOCK) + threadIdx.x; e < len; e += size_t(gridDim.x) * RED_BLOCK)
+        x[e] = fmaf(yi, __bfloat162float(v[e]), i == 0 ? 0.0f : x[e]);
+}
+
+// x = sum_{i < count} y_i V_i over a staged basis, one vector at a time in
+// the order (and with the FMA rounding) of combine_kernel, so the result is
+// the same bits.
+static cudaError_t staged_combine(Stager &sg, bool vbf16, int count, const double *y, size_t len, float *x,
+                                  cudaStream_t s)
+{
+    if (count <= 0) return cudaMemsetAsync(x, 0, len * sizeof(float), s);
+    cudaError_t e = sg.fetch(0, s);
+    if (e == cudaSuccess && 1 < count) e = sg.fetch(1, s);
+    const unsigned blocks = unsigned(std::max<size_t>(1, std::min((len + RED_BLOCK - 1) / RED_BLOCK,
+                                                                  size_t(num_sms()) * 8)));
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        const void *v = sg.vector(i, -1, s);
+        {
+            ProfScope prof(PK_COMBINE, s);
+            if (vbf16)
+                basis_axpy_kernel_bf16<<<blocks, RED_BLOCK, 0, s>>>(x, static_cast<const __nv_bfloat16 *>(v), y, i,
+                                                                      len);
+            else
+                basis_axpy_kernel_f32<<<blocks, RED_BLOCK, 0, s>>>(x, static_cast<const float *>(v), y, i, len);
+        }
+        e = cudaGetLastError();
+        if (e == cudaSuccess && i + 2 < count) e = sg.fetch(i + 2, s);
+    }
+    return e;
 }
 
 static ct_status state_alloc(const ct_geom *geom, int kmax, int basis, const ct_solve_opts &o, ct_gmres_state **out)
@@ -1364,13 +1545,15 @@ static ct_status state_alloc(const ct_geom *geom, int kmax, int basis, const ct_
             state_free(st);
             return set_error(CT_ENOMEM, "ct_bagmres_state: cudaHostAlloc(%zu bytes) for the basis failed", vb);
         }
-        void *dp = nullptr;
-        e = cudaHostGetDevicePointer(&dp, st->host_basis, 0);
+        // the kernels see only the device staging buffers; the host pointer
+        // serves the copies (and save/load)
+        st->w.V = st->host_basis;
+        e = stager_init(st);
         if (e != cudaSuccess) {
+            cudaGetLastError();
             state_free(st);
-            return cuda_error(e, "cudaHostGetDevicePointer(basis)");
+            return set_error(CT_ENOMEM, "ct_bagmres_state: the device staging buffers of a host basis failed");
         }
-        st->w.V = dp;
     }
     *out = st;
     return CT_OK;
@@ -1588,8 +1771,10 @@ ct_status ct_bagmres_state_extend(ct_gmres_state *state, int k, float *x_out_dev
     GmresWs &w = state->w;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
+    Stager *sg = state->basis == CT_BASIS_HOST ? &state->stager : nullptr;
     if (state->status == ST_RUN)
-        for (int j = state->k_done; j < k && e == cudaSuccess; ++j) e = ba_iteration(g, w, j, state->kmax, n, state->o, s);
+        for (int j = state->k_done; j < k && e == cudaSuccess; ++j)
+            e = ba_iteration(g, w, j, state->kmax, n, state->o, s, sg);
     // x = V_c y_c with c = min(k, iterations done)
     if (e == cudaSuccess) {
         ProfScope prof(PK_SMALL, s);
@@ -1597,16 +1782,24 @@ ct_status ct_bagmres_state_extend(ct_gmres_state *state, int k, float *x_out_dev
         backsolve_count_kernel<<<1, 1, 0, s>>>(w.R, w.g, w.y, w.cnt, state->kmax);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess)
+    SolverState hst;
+    std::vector<double> hres(size_t(k) + 1);
+    if (e == cudaSuccess && sg) {
+        // a staged basis streams exactly the vectors the iterate needs: learn
+        // how many first
+        e = cudaMemcpyAsync(&hst, w.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = staged_combine(*sg, w.vbf16, hst.iters < k ? hst.iters : k, w.y, n, x_out_dev, s);
+    } else if (e == cudaSuccess) {
         e = w.vbf16 ? combine_t(static_cast<const __nv_bfloat16 *>(w.V), w.ldv, state->kmax, n, w.y, w.cnt,
                                 x_out_dev, s)
                     : combine(static_cast<const float *>(w.V), w.ldv, state->kmax, n, w.y, w.cnt, x_out_dev, s);
+    }
     if (e != cudaSuccess) return cuda_error(e, "ct_bagmres_state_extend launch");
-    SolverState hst;
-    std::vector<double> hres(size_t(k) + 1);
     CT_CUDA(cudaMemcpyAsync(&hst, w.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
     CT_CUDA(cudaMemcpyAsync(hres.data(), w.resid, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, s));
     CT_CUDA(cudaStreamSynchronize(s));
+    if (sg) CT_CUDA(cudaStreamSynchronize(sg->cs));   // the host basis holds every vector on return
     state->k_done = hst.iters;
     state->status = hst.status;
     if (resid_hist) std::copy(hres.begin(), hres.end(), resid_hist);
@@ -1640,6 +1833,7 @@ ct_status ct_gmres_state_save(const ct_gmres_state *state, const char *path, voi
     h.k_done = kd;
     h.n = n;
     CT_CUDA(cudaStreamSynchronize(s));
+    if (state->stager.cs) CT_CUDA(cudaStreamSynchronize(state->stager.cs));
     CT_CUDA(cudaMemcpy(&h.st, w.st, sizeof(SolverState), cudaMemcpyDeviceToHost));
     if (h.st.iters != kd) return set_error(CT_EINVAL, "ct_gmres_state_save: the state changed since its last call");
     // the first kd columns of H and R (rows 0..kd), cs, sn, g and resid (kd + 1)

@@ -115,3 +115,22 @@ def test_load_rejects_another_geometry_and_a_small_capacity(ct, tmp_path):
     with pytest.raises(ct.CTError):
         ct.GmresState.load(g, bad, 10)
     st.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_host_basis_with_second_sweep_equals_one_solve(ct, storage):
+    """The host basis comes back to the device through a ring of buffers for
+    every MGS sweep, the optional second sweep included, and for the final
+    x = V y: still the one-call solve's bits."""
+    spec = ci.CONE_ANISO
+    g, b = scan(ct, spec, storage)
+    opts = ct.make_opts(b_kind="un", reorth=1)
+    x1 = torch.empty(spec.vol_shape, device="cuda")
+    r1 = ct.ct_bagmres_solve(g, b, 9, x1, opts)
+    st = ct.GmresState(g, 9, "host", ct.make_opts(b_kind="un", reorth=1))
+    st.start(b)
+    x = torch.empty(spec.vol_shape, device="cuda")
+    st.extend(4, x)
+    r = st.extend(9, x)
+    assert torch.equal(x, x1) and np.array_equal(r.resid, r1.resid)
+    st.close()
