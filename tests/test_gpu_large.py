@@ -64,12 +64,15 @@ def regenerate_data(meta, d):
     key = (meta["spec"]["name"], meta["data"])
     if key not in _DATA:
         spec = ci.WORKLOADS[meta["spec"]["name"]]
-        x_true = ci.phantom(spec)[0]
-        p = oracle.project_A(spec, x_true.astype(np.float64))
-        if meta["data"] == "poisson":
-            b = ci.poisson_log_data(p, i0=1e5, seed=1)
+        if meta["data"] == "smooth_gx":
+            b = ci.smooth_volume(spec, seed=3).astype(np.float32)
         else:
-            b = p.astype(np.float32)
+            x_true = ci.phantom(spec)[0]
+            p = oracle.project_A(spec, x_true.astype(np.float64))
+            if meta["data"] == "poisson":
+                b = ci.poisson_log_data(p, i0=1e5, seed=1)
+            else:
+                b = p.astype(np.float32)
         _DATA[key] = b
     b = _DATA[key]
     b64 = b.astype(np.float64).reshape(-1)
@@ -82,7 +85,6 @@ def regenerate_data(meta, d):
 
 
 def compare(parity_log, name, meta, d, x_gpu, resid_gpu, key="resid"):
-    spec = ci.WORKLOADS[meta["spec"]["name"]]
     ref = d[key]
     k = meta["k"]
     exc = EXCEPTIONS.get(name)
@@ -91,7 +93,7 @@ def compare(parity_log, name, meta, d, x_gpu, resid_gpu, key="resid"):
     tol_r = max(SOLVE_TOL, 3 * d_res) if exc else SOLVE_TOL
     r = np.asarray(resid_gpu[:k + 1], dtype=np.float64)
     err_res = float(np.max(np.abs(r - ref)) / ref[0])
-    vox = ci.sample_indices(spec.n, d["x_sample"].size, seed=meta["image_sample_seed"])
+    vox = ci.sample_indices(x_gpu.numel(), d["x_sample"].size, seed=meta["image_sample_seed"])
     xs = x_gpu.reshape(-1)[torch.from_numpy(vox).to(x_gpu.device)].double().cpu().numpy()
     err_img = float(np.linalg.norm(xs - d["x_sample"]) / np.linalg.norm(d["x_sample"]))
     err_norm = abs(float(x_gpu.double().norm()) - float(d["x_norm"])) / float(d["x_norm"])
