@@ -225,9 +225,21 @@ NCU_TRAFFIC = {
 }
 
 
-def ncu_traffic(kernel, storage, workload):
+# The same captures' load-path utilisation: l1tex__data_pipe_lsu_wavefronts
+# as a fraction of its peak (elapsed), and the passes per global load request
+# (l1tex__data_pipe_lsu_wavefronts_mem_lgds / l1tex__t_requests_pipe_lsu_mem_global_op_ld:
+# at least 4 for B's 128-bit warp loads, 1 for A's 32-bit ones).  Keyed like NCU_TRAFFIC.
+NCU_L1 = {
+    ("voxel_B", "f32", "cone_256"): ({"data_pipe_frac": 0.667, "passes_per_request": 5.33}, "ct_backproject.cu",
+                                     "5af7276986cfcebb938b5d180d4e8b0eca3afc56389e16b1ff2614291a11a982"),
+    ("joseph_A", "f32", "cone_256"): ({"data_pipe_frac": 0.453, "passes_per_request": 1.38}, "ct_project.cu",
+                                      "bb34b7769afe39007cc6cd797646a5466885e472cdc48f6d276a16769987c6e1"),
+}
+
+
+def ncu_traffic(kernel, storage, workload, table=None):
     import hashlib
-    ent = NCU_TRAFFIC.get((kernel, storage, workload))
+    ent = (NCU_TRAFFIC if table is None else table).get((kernel, storage, workload))
     if not ent:
         return None
     nbytes, src, sha = ent
@@ -426,6 +438,7 @@ def run_ours(args, world, rank, local):
     b_gather = b_samples * 16.0 / (b_ms * 1e-3) / 1e9
     gather = a_gather if dom[0] == "joseph_A" else b_gather
     traffic = ncu_traffic(dom[0], args.storage, spec.name)
+    ncu_l1 = ncu_traffic(dom[0], args.storage, spec.name, NCU_L1)
     roofline = {"kernel": dom[0], "bound": "l1_gather", "achieved": round(gather, 1), "peak": round(l1_peak, 1),
                 "unit": "GB/s", "frac": round(gather / l1_peak, 4), "traffic": traffic,
                 "peak_source": "measured: ct_measure_gather_peak (128-bit L1-hit loads, best of 5) in this run",
@@ -435,6 +448,7 @@ def run_ours(args, world, rank, local):
                                          "ms_per_launch": round(a_ms, 4)},
                             "voxel_B": {"achieved_gbs": round(b_gather, 1), "frac": round(b_gather / l1_peak, 4),
                                         "ms_per_launch": round(b_ms, 4)}},
+                "ncu_load_path": ncu_l1,
                 "derived_peak_gbs": round(l1_derived, 1),
                 "derived_peak_source": "%d SMs x 128 B/clk x 2070 MHz" % sms,
                 "hbm": {"achieved_gbs": round(achieved, 1), "peak_gbs": hbm_peak, "peak_source": peak_src,

@@ -283,9 +283,11 @@ CT_API ct_status ct_basis_combine(const float *V_dev, size_t ldv, int k, size_t 
  * that it can be extended by more iterations, saved to a file and restored
  * later.  The paper stores the growing Krylov basis on disk and adds one
  * vector per iteration (Sec. II); here the basis stays in device memory, or
- * in page-locked host memory (CT_BASIS_HOST) that the kernels read and write
- * in place, on Grace-Blackwell over NVLink-C2C, for bases larger than the
- * device memory left free.  Iterating a state k times gives bit for bit the
+ * in page-locked host memory (CT_BASIS_HOST) for bases larger than the
+ * device memory left free: the newest vector is copied out by the copy
+ * engine while the operators run, and every Gram-Schmidt sweep streams the
+ * older ones back through a ring of three device buffers (four basis vectors
+ * of device memory in all).  Iterating a state k times gives bit for bit the
  * image and residual history of ct_bagmres_solve with k iterations and the
  * same options, however the k iterations are split over calls, saved and
  * restored.  opts->tol is ignored (a state runs the iterations it is asked
