@@ -218,10 +218,10 @@ def aggregate_over_ranks(elapsed_s, iters, world, device=None):
 NCU_TRAFFIC = {
     # (kernel, storage, workload): (bytes per launch, source file,
     # sha256 of that file followed by ct_internal.cuh at capture time)
-    ("voxel_B", "f32", "cone_256"): (1415469000 + 68405504, "ct_backproject.cu",
-                                     "5af7276986cfcebb938b5d180d4e8b0eca3afc56389e16b1ff2614291a11a982"),
-    ("joseph_A", "f32", "cone_256"): (412170240 + 137536512, "ct_project.cu",
-                                      "bb34b7769afe39007cc6cd797646a5466885e472cdc48f6d276a16769987c6e1"),
+    ("voxel_B", "f32", "cone_256"): (1232532000 + 63423488, "ct_backproject.cu",
+                                     "074b8f9eab1a98b52d696e7c82a40d3350fdff1da2963aaa3433d9323b27ebf8"),
+    ("joseph_A", "f32", "cone_256"): (404909312 + 137606400, "ct_project.cu",
+                                      "1c16b5a4279276e0018650cf34780c02e10460f064168894d331332c7285794c"),
 }
 
 
@@ -230,10 +230,10 @@ NCU_TRAFFIC = {
 # (l1tex__data_pipe_lsu_wavefronts_mem_lgds / l1tex__t_requests_pipe_lsu_mem_global_op_ld:
 # at least 4 for B's 128-bit warp loads, 1 for A's 32-bit ones).  Keyed like NCU_TRAFFIC.
 NCU_L1 = {
-    ("voxel_B", "f32", "cone_256"): ({"data_pipe_frac": 0.667, "passes_per_request": 5.33}, "ct_backproject.cu",
-                                     "5af7276986cfcebb938b5d180d4e8b0eca3afc56389e16b1ff2614291a11a982"),
+    ("voxel_B", "f32", "cone_256"): ({"data_pipe_frac": 0.798, "passes_per_request": 5.33}, "ct_backproject.cu",
+                                     "074b8f9eab1a98b52d696e7c82a40d3350fdff1da2963aaa3433d9323b27ebf8"),
     ("joseph_A", "f32", "cone_256"): ({"data_pipe_frac": 0.453, "passes_per_request": 1.38}, "ct_project.cu",
-                                      "bb34b7769afe39007cc6cd797646a5466885e472cdc48f6d276a16769987c6e1"),
+                                      "1c16b5a4279276e0018650cf34780c02e10460f064168894d331332c7285794c"),
 }
 
 

@@ -483,6 +483,110 @@ __global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, cons
     }
 }
 
+// The back-projector for 3D scans.  A block of 32 x TY threads owns a 32 x TY
+// tile of (x, y) columns and ZC consecutive z (ZC = 16: the column's
+// projection is computed once per view for 16 samples); MINB blocks are
+// resident per SM.  With PASSES = 2 the view loop runs twice, once over the
+// views whose lanes run along x and once over those along y, into one set of
+// ZC accumulators (half the registers of two sets); the tile in shared
+// memory merges the two lane mappings.  A warp covers a 4 x 8 patch of
+// columns, 4 lanes along the axis nearer the central ray (see above).  Small
+// blocks (256 threads, 4 per SM) keep 32 warps resident like one 1024-thread
+// block, but the blocks' starts and ends (view table, tile merge, stores)
+// overlap other blocks' view loops instead of idling the SM: 4.34 ms at 256^3
+// against 5.09 ms for voxel_B_kernel with 8-slice runs.
+template <int ZC, int TY, int MINB, int PASSES, bool BF, bool DIFF>
+__global__ void __launch_bounds__(32 * TY, MINB) voxel_B_slab_kernel(GeomDev g, const void *__restrict__ ypad,
+                                                                     float *__restrict__ x,
+                                                                     const int *__restrict__ stop)
+{
+    static_assert(TY % 8 == 0, "a warp's 4 x 8 patch must tile the 32 x TY block both ways");
+    if (stop && *stop) return;
+    extern __shared__ float4 sviews[];   // 2 per view, then the tile
+    float(*tile)[TY][B_TILE + 1] = reinterpret_cast<float(*)[TY][B_TILE + 1]>(sviews + 2 * g.n_views);
+    const int l = threadIdx.x, w = threadIdx.y;
+    const int tid = w * 32 + l;
+    const float4 *vt = reinterpret_cast<const float4 *>(g.viewB);
+    for (int i = tid; i < 2 * g.n_views; i += 32 * TY) sviews[i] = __ldg(vt + i);
+    const int X0 = blockIdx.x * 32, Y0 = blockIdx.y * TY;
+    const int iz0 = blockIdx.z * ZC;
+    const float zfirst = (float(iz0) - g.cz) * g.vox;
+    const int tax = (w % 8) * 4 + l % 4, tay = (w / 8) * 8 + l / 4;           // lanes along x
+    const int tby = (w % (TY / 4)) * 4 + l % 4, tbx = (w / (TY / 4)) * 8 + l / 4;   // lanes along y
+    const int ax = min(X0 + tax, g.nx - 1), ay = min(Y0 + tay, g.ny - 1);
+    const int bx = min(X0 + tbx, g.nx - 1), by = min(Y0 + tby, g.ny - 1);
+    const float axc = (float(ax) - g.cx) * g.vox, ayc = (float(ay) - g.cy) * g.vox;
+    const float bxc = (float(bx) - g.cx) * g.vox, byc = (float(by) - g.cy) * g.vox;
+    const int view_stride = g.nvp * g.pitchU;
+    const int pitch = g.pitchU;
+    __syncthreads();
+    float accA[ZC], accB[PASSES == 1 ? ZC : 1];
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) accA[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < (PASSES == 1 ? ZC : 1); ++k) accB[k] = 0.0f;
+#pragma unroll 1
+    for (int pass = 0; pass < PASSES; ++pass) {
+        if (PASSES == 2 && pass == 1) {
+#pragma unroll
+            for (int k = 0; k < ZC; ++k) accA[k] = 0.0f;
+        }
+        for (int s = 0; s < g.n_views; ++s) {
+            const float4 p = sviews[2 * s], q = sviews[2 * s + 1];
+            const bool xl = fabsf(p.w) <= fabsf(q.x);
+            if (PASSES == 2 && xl != (pass == 0)) continue;
+            const ColumnView c = column_view(g, p, q, xl ? axc : bxc, xl ? ayc : byc, zfirst);
+            if (c.skip) continue;
+            float r[ZC];
+            column_samples<ZC, BF, DIFF>(g, ypad, c, s, view_stride, pitch, r);
+            if (PASSES == 2 || xl)
+                accumulate<ZC, DIFF>(accA, r, c.w);
+            else
+                accumulate<(PASSES == 1 ? ZC : 1), DIFF>(accB, *reinterpret_cast<float(*)[PASSES == 1 ? ZC : 1]>(r),
+                                                          c.w);
+        }
+        if (PASSES == 2) {
+            if (pass == 0) {
+#pragma unroll
+                for (int k = 0; k < ZC; ++k) tile[k][tay][tax] = accA[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < ZC; ++k) tile[k][tby][tbx] += accA[k];
+            }
+            __syncthreads();
+        }
+    }
+    if (PASSES == 1) {
+#pragma unroll
+        for (int k = 0; k < ZC; ++k) tile[k][tay][tax] = accA[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < (PASSES == 1 ? ZC : 1); ++k) tile[k][tby][tbx] += accB[k];
+        __syncthreads();
+    }
+    const int ix = X0 + l, iy = Y0 + w;
+    if (ix >= g.nx || iy >= g.ny) return;
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) {
+        const int iz = iz0 + k;
+        if (iz < g.nz) x[(size_t(iz) * g.ny + iy) * g.nx + ix] = tile[k][w][l];
+    }
+}
+
+template <int ZC, int TY, int MINB, int PASSES, bool BF, bool DIFF>
+static cudaError_t launch_voxel_B_slab(const GeomDev &g, const float *ypad, float *x, const int *stop,
+                                       cudaStream_t st)
+{
+    dim3 block(32, TY);
+    const size_t smem = size_t(g.n_views) * 2 * sizeof(float4) + size_t(ZC) * TY * (B_TILE + 1) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(voxel_B_slab_kernel<ZC, TY, MINB, PASSES, BF, DIFF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    dim3 grid((g.nx + 31) / 32, (g.ny + TY - 1) / TY, (g.nz + ZC - 1) / ZC);
+    voxel_B_slab_kernel<ZC, TY, MINB, PASSES, BF, DIFF><<<grid, block, smem, st>>>(g, ypad, x, stop);
+    return cudaGetLastError();
+}
+
 // The same sum in two passes over the views, one per lane orientation, into
 // one set of ZC accumulators; the tile that merges the two mappings sits in
 // dynamic shared memory after the view table.  Half the accumulator registers
@@ -598,6 +702,9 @@ cudaError_t launch_voxel_B(const GeomDev &g, const float *ypad, float *x, const 
 {
     ProfScope prof(PK_VOXEL_B, st);
     if (g.nz == 1) return launch_voxel_B_z<1, 32>(g, ypad, x, stop, st, form);
+    if (!g.sino_bf16)
+        return form == QUAD_ROWDIFF ? launch_voxel_B_slab<B_ZC_SLAB, 8, 4, 2, false, true>(g, ypad, x, stop, st)
+                                    : launch_voxel_B_slab<B_ZC_SLAB, 8, 4, 2, false, false>(g, ypad, x, stop, st);
     if (g.sino_bf16 && g.nz >= B_ZC_2PASS)
         return launch_voxel_B_2pass<B_ZC_2PASS, true>(g, ypad, x, stop, st);
     return launch_voxel_B_z<B_ZC, B_PA>(g, ypad, x, stop, st, form);
