@@ -19,8 +19,11 @@ pytestmark = pytest.mark.gpu
 
 OP_TOL = 1e-5
 
+# cone_z40: 40 slices, so the last 16-slice run of the 3D back-projector
+# passes nz by 8 (the row margin covers it); cone_aniso: 36 rows of columns
+# and 28 slices, ragged against its 32 x 8 x 16 tiles
 SMALL = [ci.CONE_SMALL, ci.CONE_ANISO, ci.CONE_THIN, ci.PAR2D_ANISO, ci.PAR2D_64, ci.CONE_GRAD32,
-         ci.CONE_512_CUT64]
+         ci.CONE_512_CUT64, ci.CONE_Z40]
 
 
 @pytest.fixture(scope="module")
