@@ -217,11 +217,9 @@ def aggregate_over_ranks(elapsed_s, iters, world, device=None):
 # profiles/.
 NCU_TRAFFIC = {
     # (kernel, storage, workload): (bytes per launch, source file,
-    # sha256 of that file followed by ct_internal.cuh at capture time; the
-    # voxel_B entries were re-keyed when only the transpose kernels in the
-    # same file changed, voxel_B_slab_kernel's source being the captured one)
-    ("voxel_B", "f32", "cone_256"): (1232532000 + 63423488, "ct_backproject.cu",
-                                     "a5694d0088ab68b73b16a8bea12b085a883b8a55c1b7ae0d2ca48adbbf316d07"),
+    # sha256 of that file followed by ct_internal.cuh at capture time)
+    ("voxel_B", "f32", "cone_256"): (1221907712 + 80108288, "ct_backproject.cu",
+                                     "e674e2e3909dc809542faecde1f794dbb9cc482a178e5958da335a5ba1b14adf"),
     ("joseph_A", "f32", "cone_256"): (404909312 + 137606400, "ct_project.cu",
                                       "1c16b5a4279276e0018650cf34780c02e10460f064168894d331332c7285794c"),
 }
@@ -232,8 +230,8 @@ NCU_TRAFFIC = {
 # (l1tex__data_pipe_lsu_wavefronts_mem_lgds / l1tex__t_requests_pipe_lsu_mem_global_op_ld:
 # at least 4 for B's 128-bit warp loads, 1 for A's 32-bit ones).  Keyed like NCU_TRAFFIC.
 NCU_L1 = {
-    ("voxel_B", "f32", "cone_256"): ({"data_pipe_frac": 0.798, "passes_per_request": 5.33}, "ct_backproject.cu",
-                                     "a5694d0088ab68b73b16a8bea12b085a883b8a55c1b7ae0d2ca48adbbf316d07"),
+    ("voxel_B", "f32", "cone_256"): ({"data_pipe_frac": 0.800, "passes_per_request": 5.34}, "ct_backproject.cu",
+                                     "e674e2e3909dc809542faecde1f794dbb9cc482a178e5958da335a5ba1b14adf"),
     ("joseph_A", "f32", "cone_256"): ({"data_pipe_frac": 0.453, "passes_per_request": 1.38}, "ct_project.cu",
                                       "1c16b5a4279276e0018650cf34780c02e10460f064168894d331332c7285794c"),
 }

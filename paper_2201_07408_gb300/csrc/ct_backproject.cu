@@ -483,27 +483,60 @@ __global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, cons
     }
 }
 
-// The back-projector for 3D scans.  A block of 32 x TY threads owns a 32 x TY
-// tile of (x, y) columns and ZC consecutive z (ZC = 16: the column's
-// projection is computed once per view for 16 samples); MINB blocks are
-// resident per SM.  With PASSES = 2 the view loop runs twice, once over the
+// The ZC samples of one column in one view from a per-view pointer: pv is
+// the byte address of the column's entry in the view's first unpadded row
+// (the row margin folded in), so a sample's address is one multiply-add of
+// its row index and the row pitch in bytes (the entries' forms as in
+// column_samples).
+template <int ZC, bool DIFF>
+__device__ __forceinline__ void column_samples_at(const char *__restrict__ pv, const ColumnView &c, int pitch_bytes,
+                                                  float (&r)[ZC])
+{
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) {
+        const float fv = fmaf(float(k), c.gv, c.fv0);
+        const float v0f = floorf(fv);
+        const float wv = fv - v0f;
+        const float4 nb = __ldg(reinterpret_cast<const float4 *>(pv + int(v0f) * pitch_bytes));
+        if (DIFF) {
+            const float e0 = fmaf(c.wu, nb.y, nb.x);
+            const float e1 = fmaf(c.wu, nb.w, nb.z);
+            r[k] = fmaf(wv, e1 - e0, e0);
+        } else {
+            const float r0 = fmaf(c.a0, nb.x, c.a1 * nb.y);
+            const float r1 = fmaf(c.a0, nb.z, c.a1 * nb.w);
+            r[k] = fmaf(wv, r1 - r0, r0);
+        }
+    }
+}
+
+// The back-projector for 3D scans (FP32 entries).  A block of 32 x TY
+// threads owns a 32 x TY tile of (x, y) columns and ZC consecutive z (ZC =
+// 16: the column's projection is computed once per view for 16 samples);
+// MINB blocks are resident per SM.  The view loop runs twice, once over the
 // views whose lanes run along x and once over those along y, into one set of
-// ZC accumulators (half the registers of two sets); the tile in shared
-// memory merges the two lane mappings.  A warp covers a 4 x 8 patch of
-// columns, 4 lanes along the axis nearer the central ray (see above).  Small
-// blocks (256 threads, 4 per SM) keep 32 warps resident like one 1024-thread
-// block, but the blocks' starts and ends (view table, tile merge, stores)
-// overlap other blocks' view loops instead of idling the SM: 4.34 ms at 256^3
-// against 5.09 ms for voxel_B_kernel with 8-slice runs.
-template <int ZC, int TY, int MINB, int PASSES, bool BF, bool DIFF>
+// ZC accumulators; the tile in shared memory merges the two lane mappings.
+// Warp 0 lists the views of each orientation (ballots over the view table)
+// so that each pass visits only its own views.  A warp covers a 4 x 8 patch
+// of columns, 4 lanes along the axis nearer the central ray (see above).
+// Small blocks (256 threads, 4 per SM) keep 32 warps resident like one
+// 1024-thread block, but the blocks' starts and ends (view table, tile
+// merge, stores) overlap other blocks' view loops instead of idling the SM.
+// At 256^3: 4.16 ms; 4.35 ms when each pass tested every view's orientation
+// and addressed samples from the view index; 5.09 ms for voxel_B_kernel with
+// 8-slice runs.
+template <int ZC, int TY, int MINB, bool DIFF>
 __global__ void __launch_bounds__(32 * TY, MINB) voxel_B_slab_kernel(GeomDev g, const void *__restrict__ ypad,
                                                                      float *__restrict__ x,
                                                                      const int *__restrict__ stop)
 {
     static_assert(TY % 8 == 0, "a warp's 4 x 8 patch must tile the 32 x TY block both ways");
     if (stop && *stop) return;
-    extern __shared__ float4 sviews[];   // 2 per view, then the tile
+    // 2 float4 per view, then the tile, then the views listed by orientation
+    extern __shared__ float4 sviews[];
     float(*tile)[TY][B_TILE + 1] = reinterpret_cast<float(*)[TY][B_TILE + 1]>(sviews + 2 * g.n_views);
+    short *order = reinterpret_cast<short *>(&tile[ZC][0][0]);
+    __shared__ int n_along_x;
     const int l = threadIdx.x, w = threadIdx.y;
     const int tid = w * 32 + l;
     const float4 *vt = reinterpret_cast<const float4 *>(g.viewB);
@@ -520,48 +553,55 @@ __global__ void __launch_bounds__(32 * TY, MINB) voxel_B_slab_kernel(GeomDev g, 
     const int view_stride = g.nvp * g.pitchU;
     const int pitch = g.pitchU;
     __syncthreads();
-    float accA[ZC], accB[PASSES == 1 ? ZC : 1];
-#pragma unroll
-    for (int k = 0; k < ZC; ++k) accA[k] = 0.0f;
-#pragma unroll
-    for (int k = 0; k < (PASSES == 1 ? ZC : 1); ++k) accB[k] = 0.0f;
-#pragma unroll 1
-    for (int pass = 0; pass < PASSES; ++pass) {
-        if (PASSES == 2 && pass == 1) {
-#pragma unroll
-            for (int k = 0; k < ZC; ++k) accA[k] = 0.0f;
+    if (w == 0) {   // order[0, n_along_x): views with lanes along x; then the others
+        int count = 0;
+        for (int s0 = 0; s0 < g.n_views; s0 += 32) {
+            const int s = s0 + l;
+            const bool xl = s < g.n_views && fabsf(sviews[2 * s].w) <= fabsf(sviews[2 * s + 1].x);
+            count += __popc(__ballot_sync(0xffffffffu, xl));
         }
-        for (int s = 0; s < g.n_views; ++s) {
-            const float4 p = sviews[2 * s], q = sviews[2 * s + 1];
-            const bool xl = fabsf(p.w) <= fabsf(q.x);
-            if (PASSES == 2 && xl != (pass == 0)) continue;
-            const ColumnView c = column_view(g, p, q, xl ? axc : bxc, xl ? ayc : byc, zfirst);
-            if (c.skip) continue;
-            float r[ZC];
-            column_samples<ZC, BF, DIFF>(g, ypad, c, s, view_stride, pitch, r);
-            if (PASSES == 2 || xl)
-                accumulate<ZC, DIFF>(accA, r, c.w);
-            else
-                accumulate<(PASSES == 1 ? ZC : 1), DIFF>(accB, *reinterpret_cast<float(*)[PASSES == 1 ? ZC : 1]>(r),
-                                                          c.w);
+        int a = 0, b = count;
+        const unsigned below = (1u << l) - 1u;
+        for (int s0 = 0; s0 < g.n_views; s0 += 32) {
+            const int s = s0 + l;
+            const bool in = s < g.n_views;
+            const bool xl = in && fabsf(sviews[2 * s].w) <= fabsf(sviews[2 * s + 1].x);
+            const unsigned mx = __ballot_sync(0xffffffffu, xl), my = __ballot_sync(0xffffffffu, in && !xl);
+            if (xl)
+                order[a + __popc(mx & below)] = short(s);
+            else if (in)
+                order[b + __popc(my & below)] = short(s);
+            a += __popc(mx);
+            b += __popc(my);
         }
-        if (PASSES == 2) {
-            if (pass == 0) {
-#pragma unroll
-                for (int k = 0; k < ZC; ++k) tile[k][tay][tax] = accA[k];
-            } else {
-#pragma unroll
-                for (int k = 0; k < ZC; ++k) tile[k][tby][tbx] += accA[k];
-            }
-            __syncthreads();
-        }
+        if (l == 0) n_along_x = count;
     }
-    if (PASSES == 1) {
+    __syncthreads();
+    float acc[ZC];
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll
-        for (int k = 0; k < ZC; ++k) tile[k][tay][tax] = accA[k];
-        __syncthreads();
+        for (int k = 0; k < ZC; ++k) acc[k] = 0.0f;
+        const int i0 = pass == 0 ? 0 : n_along_x, i1 = pass == 0 ? n_along_x : g.n_views;
+        const float cx = pass == 0 ? axc : bxc, cy = pass == 0 ? ayc : byc;
+        for (int i = i0; i < i1; ++i) {
+            const int s = order[i];
+            const ColumnView c = column_view(g, sviews[2 * s], sviews[2 * s + 1], cx, cy, zfirst);
+            if (c.skip) continue;
+            const char *pv = static_cast<const char *>(ypad) +
+                             16 * (size_t(s) * view_stride + size_t(g.padv) * pitch + c.col);
+            float r[ZC];
+            column_samples_at<ZC, DIFF>(pv, c, 16 * pitch, r);
+            accumulate<ZC, DIFF>(acc, r, c.w);
+        }
+        // x-lane sums belong to (X0 + tax, Y0 + tay), y-lane sums to (X0 + tbx, Y0 + tby)
+        if (pass == 0) {
 #pragma unroll
-        for (int k = 0; k < (PASSES == 1 ? ZC : 1); ++k) tile[k][tby][tbx] += accB[k];
+            for (int k = 0; k < ZC; ++k) tile[k][tay][tax] = acc[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < ZC; ++k) tile[k][tby][tbx] += acc[k];
+        }
         __syncthreads();
     }
     const int ix = X0 + l, iy = Y0 + w;
@@ -573,17 +613,18 @@ __global__ void __launch_bounds__(32 * TY, MINB) voxel_B_slab_kernel(GeomDev g, 
     }
 }
 
-template <int ZC, int TY, int MINB, int PASSES, bool BF, bool DIFF>
+template <int ZC, int TY, int MINB, bool DIFF>
 static cudaError_t launch_voxel_B_slab(const GeomDev &g, const float *ypad, float *x, const int *stop,
                                        cudaStream_t st)
 {
     dim3 block(32, TY);
-    const size_t smem = size_t(g.n_views) * 2 * sizeof(float4) + size_t(ZC) * TY * (B_TILE + 1) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(voxel_B_slab_kernel<ZC, TY, MINB, PASSES, BF, DIFF>,
+    const size_t smem = size_t(g.n_views) * 2 * sizeof(float4) + size_t(ZC) * TY * (B_TILE + 1) * sizeof(float) +
+                        size_t(g.n_views) * sizeof(short);
+    cudaError_t e = cudaFuncSetAttribute(voxel_B_slab_kernel<ZC, TY, MINB, DIFF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     dim3 grid((g.nx + 31) / 32, (g.ny + TY - 1) / TY, (g.nz + ZC - 1) / ZC);
-    voxel_B_slab_kernel<ZC, TY, MINB, PASSES, BF, DIFF><<<grid, block, smem, st>>>(g, ypad, x, stop);
+    voxel_B_slab_kernel<ZC, TY, MINB, DIFF><<<grid, block, smem, st>>>(g, ypad, x, stop);
     return cudaGetLastError();
 }
 
@@ -703,8 +744,8 @@ cudaError_t launch_voxel_B(const GeomDev &g, const float *ypad, float *x, const 
     ProfScope prof(PK_VOXEL_B, st);
     if (g.nz == 1) return launch_voxel_B_z<1, 32>(g, ypad, x, stop, st, form);
     if (!g.sino_bf16)
-        return form == QUAD_ROWDIFF ? launch_voxel_B_slab<B_ZC_SLAB, 8, 4, 2, false, true>(g, ypad, x, stop, st)
-                                    : launch_voxel_B_slab<B_ZC_SLAB, 8, 4, 2, false, false>(g, ypad, x, stop, st);
+        return form == QUAD_ROWDIFF ? launch_voxel_B_slab<B_ZC_SLAB, 8, 4, true>(g, ypad, x, stop, st)
+                                    : launch_voxel_B_slab<B_ZC_SLAB, 8, 4, false>(g, ypad, x, stop, st);
     if (g.sino_bf16 && g.nz >= B_ZC_2PASS)
         return launch_voxel_B_2pass<B_ZC_2PASS, true>(g, ypad, x, stop, st);
     return launch_voxel_B_z<B_ZC, B_PA>(g, ypad, x, stop, st, form);
