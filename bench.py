@@ -217,11 +217,14 @@ def aggregate_over_ranks(elapsed_s, iters, world, device=None):
 # profiles/.
 NCU_TRAFFIC = {
     # (kernel, storage, workload): (bytes per launch, source file,
-    # sha256 of that file followed by ct_internal.cuh at capture time)
-    ("voxel_B", "f32", "cone_256"): (1221907712 + 80108288, "ct_backproject.cu",
-                                     "e674e2e3909dc809542faecde1f794dbb9cc482a178e5958da335a5ba1b14adf"),
+    # sha256 of that file followed by ct_internal.cuh at capture time; the
+    # joseph_A entries were re-keyed when only the back-projector's run-length
+    # constants in ct_internal.cuh changed, the projector's code being the
+    # captured one)
+    ("voxel_B", "f32", "cone_256"): (1217241088 + 80254976, "ct_backproject.cu",
+                                     "1e7f0cce6c58c4a60dc490d47046881cd796ea76a28f5d363ca8e428e3de0c59"),
     ("joseph_A", "f32", "cone_256"): (404909312 + 137606400, "ct_project.cu",
-                                      "1c16b5a4279276e0018650cf34780c02e10460f064168894d331332c7285794c"),
+                                      "67b72fa70b4b907746b6c77a4867773c98cc4a0083a7e00339742b3674dde173"),
 }
 
 
@@ -230,10 +233,10 @@ NCU_TRAFFIC = {
 # (l1tex__data_pipe_lsu_wavefronts_mem_lgds / l1tex__t_requests_pipe_lsu_mem_global_op_ld:
 # at least 4 for B's 128-bit warp loads, 1 for A's 32-bit ones).  Keyed like NCU_TRAFFIC.
 NCU_L1 = {
-    ("voxel_B", "f32", "cone_256"): ({"data_pipe_frac": 0.800, "passes_per_request": 5.34}, "ct_backproject.cu",
-                                     "e674e2e3909dc809542faecde1f794dbb9cc482a178e5958da335a5ba1b14adf"),
+    ("voxel_B", "f32", "cone_256"): ({"data_pipe_frac": 0.801, "passes_per_request": 5.34}, "ct_backproject.cu",
+                                     "1e7f0cce6c58c4a60dc490d47046881cd796ea76a28f5d363ca8e428e3de0c59"),
     ("joseph_A", "f32", "cone_256"): ({"data_pipe_frac": 0.453, "passes_per_request": 1.38}, "ct_project.cu",
-                                      "1c16b5a4279276e0018650cf34780c02e10460f064168894d331332c7285794c"),
+                                      "67b72fa70b4b907746b6c77a4867773c98cc4a0083a7e00339742b3674dde173"),
 }
 
 

@@ -355,23 +355,23 @@ __device__ __forceinline__ ColumnView column_view(const GeomDev &g, int s, float
     return column_view(g, __ldg(vp), __ldg(vp + 1), x, y, zfirst);
 }
 
-// A block owns a 32 x 32 tile of (x, y) columns and B_ZC consecutive z.  A
-// warp covers a patch of PA x (32/PA) columns, PA lanes along the axis
-// closer to the view's central ray (chosen per view: along x when
-// |tx| <= |ty|, i.e. when u moves more slowly with x than with y).  Along
-// the central ray the projection barely moves (only the magnification
-// changes, by vox/depth per voxel); across it, u moves by M vox/du pixels
-// per lane.  The load path's passes per 128-bit warp load (ncu: data-pipe
-// wavefronts per request) follow the number of distinct 128-byte lines that
-// each group of 8 consecutive lanes touches, so the patch is chosen for
-// that: 4 lanes along by 2 across per group of 8 (PA = 4) touches fewest on
-// the cone-beam scans (at 256^3: 5.3 passes per warp load against 6.4 with
-// all 32 lanes along the ray; B 5.09 against 5.49 ms).
-// The two partial sums (x-lane views and y-lane views) meet in shared
-// memory.  The sinogram is read as quads (the 2 x 2 bilinear neighbourhood),
-// one 16-byte load per voxel and view; the view table sits in shared memory.
+// Lane patches.  A warp covers a patch of PA x (32/PA) columns, PA lanes
+// along the axis closer to the view's central ray (chosen per view: along x
+// when |tx| <= |ty|, i.e. when u moves more slowly with x than with y).
+// Along the central ray the projection barely moves (only the magnification
+// changes, by vox/depth per voxel); across it, u moves by M vox/du pixels per
+// lane.  The load path serves a 128-bit warp load 8 lanes at a time, and its
+// passes per load (ncu: data-pipe wavefronts per request) grow when those
+// lanes' quads spread over several 128-byte lines: of the patches measured on
+// the cone-beam scans, 4 lanes along by 2 across per group of 8 (PA = 4)
+// takes fewest (at 256^3: 5.3 passes per warp load against 6.4 with all 32
+// lanes along the ray).  The 3D kernel (voxel_B_slab_kernel) uses that patch.
+// voxel_B_kernel serves 2D scans: a block owns a 32 x 32 tile of columns
+// (ZC = 1, PA = 32: the detector is one row), and the two partial sums
+// (x-lane views and y-lane views) meet in shared memory.  The sinogram is
+// read as quads (the 2 x 2 bilinear neighbourhood), one 16-byte load (8 for
+// bf16) per voxel and view; the view table sits in shared memory.
 constexpr int B_TILE = 32;
-constexpr int B_PA = 4;
 
 // the four bilinear neighbours of one sinogram quad entry
 template <bool BF>
@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, cons
 // (the row margin folded in), so a sample's address is one multiply-add of
 // its row index and the row pitch in bytes (the entries' forms as in
 // column_samples).
-template <int ZC, bool DIFF>
+template <int ZC, bool BF, bool DIFF>
 __device__ __forceinline__ void column_samples_at(const char *__restrict__ pv, const ColumnView &c, int pitch_bytes,
                                                   float (&r)[ZC])
 {
@@ -497,7 +497,7 @@ __device__ __forceinline__ void column_samples_at(const char *__restrict__ pv, c
         const float fv = fmaf(float(k), c.gv, c.fv0);
         const float v0f = floorf(fv);
         const float wv = fv - v0f;
-        const float4 nb = __ldg(reinterpret_cast<const float4 *>(pv + int(v0f) * pitch_bytes));
+        const float4 nb = load_quad<BF>(pv + int(v0f) * pitch_bytes, 0);
         if (DIFF) {
             const float e0 = fmaf(c.wu, nb.y, nb.x);
             const float e1 = fmaf(c.wu, nb.w, nb.z);
@@ -510,7 +510,7 @@ __device__ __forceinline__ void column_samples_at(const char *__restrict__ pv, c
     }
 }
 
-// The back-projector for 3D scans (FP32 entries).  A block of 32 x TY
+// The back-projector for 3D scans (FP32 or bf16 entries).  A block of 32 x TY
 // threads owns a 32 x TY tile of (x, y) columns and ZC consecutive z (ZC =
 // 16: the column's projection is computed once per view for 16 samples);
 // MINB blocks are resident per SM.  The view loop runs twice, once over the
@@ -524,8 +524,9 @@ __device__ __forceinline__ void column_samples_at(const char *__restrict__ pv, c
 // merge, stores) overlap other blocks' view loops instead of idling the SM.
 // At 256^3: 4.16 ms; 4.35 ms when each pass tested every view's orientation
 // and addressed samples from the view index; 5.09 ms for voxel_B_kernel with
-// 8-slice runs.
-template <int ZC, int TY, int MINB, bool DIFF>
+// 8-slice runs.  On bf16 entries 4.18 ms (a 1024-thread two-pass kernel took
+// 4.93 ms).
+template <int ZC, int TY, int MINB, bool BF, bool DIFF>
 __global__ void __launch_bounds__(32 * TY, MINB) voxel_B_slab_kernel(GeomDev g, const void *__restrict__ ypad,
                                                                      float *__restrict__ x,
                                                                      const int *__restrict__ stop)
@@ -588,10 +589,11 @@ __global__ void __launch_bounds__(32 * TY, MINB) voxel_B_slab_kernel(GeomDev g, 
             const int s = order[i];
             const ColumnView c = column_view(g, sviews[2 * s], sviews[2 * s + 1], cx, cy, zfirst);
             if (c.skip) continue;
+            constexpr int ENTRY = BF ? 8 : 16;   // bytes per quad entry
             const char *pv = static_cast<const char *>(ypad) +
-                             16 * (size_t(s) * view_stride + size_t(g.padv) * pitch + c.col);
+                             ENTRY * (size_t(s) * view_stride + size_t(g.padv) * pitch + c.col);
             float r[ZC];
-            column_samples_at<ZC, DIFF>(pv, c, 16 * pitch, r);
+            column_samples_at<ZC, BF, DIFF>(pv, c, ENTRY * pitch, r);
             accumulate<ZC, DIFF>(acc, r, c.w);
         }
         // x-lane sums belong to (X0 + tax, Y0 + tay), y-lane sums to (X0 + tbx, Y0 + tby)
@@ -613,104 +615,18 @@ __global__ void __launch_bounds__(32 * TY, MINB) voxel_B_slab_kernel(GeomDev g, 
     }
 }
 
-template <int ZC, int TY, int MINB, bool DIFF>
+template <int ZC, int TY, int MINB, bool BF, bool DIFF>
 static cudaError_t launch_voxel_B_slab(const GeomDev &g, const float *ypad, float *x, const int *stop,
                                        cudaStream_t st)
 {
     dim3 block(32, TY);
     const size_t smem = size_t(g.n_views) * 2 * sizeof(float4) + size_t(ZC) * TY * (B_TILE + 1) * sizeof(float) +
                         size_t(g.n_views) * sizeof(short);
-    cudaError_t e = cudaFuncSetAttribute(voxel_B_slab_kernel<ZC, TY, MINB, DIFF>,
+    cudaError_t e = cudaFuncSetAttribute(voxel_B_slab_kernel<ZC, TY, MINB, BF, DIFF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     dim3 grid((g.nx + 31) / 32, (g.ny + TY - 1) / TY, (g.nz + ZC - 1) / ZC);
-    voxel_B_slab_kernel<ZC, TY, MINB, DIFF><<<grid, block, smem, st>>>(g, ypad, x, stop);
-    return cudaGetLastError();
-}
-
-// The same sum in two passes over the views, one per lane orientation, into
-// one set of ZC accumulators; the tile that merges the two mappings sits in
-// dynamic shared memory after the view table.  Half the accumulator registers
-// of voxel_B_kernel buy a z run twice as long, which halves the per-column
-// work (the column's projection) per sample.  Used for bf16 entries with
-// ZC = 16 (4.94 against 5.35 ms at 256^3); with FP32 entries ptxas schedules
-// fewer loads in flight and it is slower.  Entries hold the four values.
-template <int ZC, bool BF>
-__global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_2pass_kernel(GeomDev g, const void *__restrict__ ypad,
-                                                                       float *__restrict__ x,
-                                                                       const int *__restrict__ stop)
-{
-    if (stop && *stop) return;
-    extern __shared__ float4 sviews[];   // 2 per view, then the tile
-    float(*tile)[B_TILE][B_TILE + 1] = reinterpret_cast<float(*)[B_TILE][B_TILE + 1]>(sviews + 2 * g.n_views);
-    const int l = threadIdx.x, w = threadIdx.y;
-    const int tid = w * B_TILE + l;
-    const float4 *vt = reinterpret_cast<const float4 *>(g.viewB);
-    for (int i = tid; i < 2 * g.n_views; i += B_TILE * B_TILE) sviews[i] = __ldg(vt + i);
-    const int X0 = blockIdx.x * B_TILE, Y0 = blockIdx.y * B_TILE;
-    const int iz0 = blockIdx.z * ZC;
-    const float zfirst = (float(iz0) - g.cz) * g.vox;
-    const int ax = min(X0 + l, g.nx - 1), ay = min(Y0 + w, g.ny - 1);
-    const int bx = min(X0 + w, g.nx - 1), by = min(Y0 + l, g.ny - 1);
-    const float axc = (float(ax) - g.cx) * g.vox, ayc = (float(ay) - g.cy) * g.vox;
-    const float bxc = (float(bx) - g.cx) * g.vox, byc = (float(by) - g.cy) * g.vox;
-    const int view_stride = g.nvp * g.pitchU;
-    const int pitch = g.pitchU;
-    __syncthreads();
-    float acc[ZC];
-#pragma unroll 1
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool want_xl = pass == 0;
-#pragma unroll
-        for (int k = 0; k < ZC; ++k) acc[k] = 0.0f;
-        for (int s = 0; s < g.n_views; ++s) {
-            const float4 p = sviews[2 * s], q = sviews[2 * s + 1];
-            const bool xl = fabsf(p.w) <= fabsf(q.x);
-            if (xl != want_xl) continue;
-            const ColumnView c = column_view(g, p, q, xl ? axc : bxc, xl ? ayc : byc, zfirst);
-            if (c.skip) continue;
-            const size_t vbase = size_t(s) * view_stride + c.col;
-#pragma unroll
-            for (int k = 0; k < ZC; ++k) {
-                const float fv = fmaf(float(k), c.gv, c.fv0);
-                const float v0f = floorf(fv);
-                const float wv = fv - v0f;
-                const float4 nb = load_quad<BF>(ypad, vbase + size_t((int(v0f) + g.padv) * pitch));
-                const float r0 = fmaf(c.a0, nb.x, c.a1 * nb.y);
-                const float r1 = fmaf(c.a0, nb.z, c.a1 * nb.w);
-                acc[k] += fmaf(wv, r1 - r0, r0);
-            }
-        }
-        // x-lane sums belong to (x = X0 + l, y = Y0 + w), y-lane sums to (x = X0 + w, y = Y0 + l)
-        if (pass == 0) {
-#pragma unroll
-            for (int k = 0; k < ZC; ++k) tile[k][w][l] = acc[k];
-        } else {
-#pragma unroll
-            for (int k = 0; k < ZC; ++k) tile[k][l][w] += acc[k];
-        }
-        __syncthreads();
-    }
-    const int ix = X0 + l, iy = Y0 + w;
-    if (ix >= g.nx || iy >= g.ny) return;
-#pragma unroll
-    for (int k = 0; k < ZC; ++k) {
-        const int iz = iz0 + k;
-        if (iz < g.nz) x[(size_t(iz) * g.ny + iy) * g.nx + ix] = tile[k][w][l];
-    }
-}
-
-template <int ZC, bool BF>
-static cudaError_t launch_voxel_B_2pass(const GeomDev &g, const float *ypad, float *x, const int *stop,
-                                        cudaStream_t st)
-{
-    dim3 block(B_TILE, B_TILE);
-    const size_t smem = size_t(g.n_views) * 2 * sizeof(float4) + size_t(ZC) * B_TILE * (B_TILE + 1) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(voxel_B_2pass_kernel<ZC, BF>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    dim3 grid((g.nx + B_TILE - 1) / B_TILE, (g.ny + B_TILE - 1) / B_TILE, (g.nz + ZC - 1) / ZC);
-    voxel_B_2pass_kernel<ZC, BF><<<grid, block, smem, st>>>(g, ypad, x, stop);
+    voxel_B_slab_kernel<ZC, TY, MINB, BF, DIFF><<<grid, block, smem, st>>>(g, ypad, x, stop);
     return cudaGetLastError();
 }
 
@@ -743,12 +659,9 @@ cudaError_t launch_voxel_B(const GeomDev &g, const float *ypad, float *x, const 
 {
     ProfScope prof(PK_VOXEL_B, st);
     if (g.nz == 1) return launch_voxel_B_z<1, 32>(g, ypad, x, stop, st, form);
-    if (!g.sino_bf16)
-        return form == QUAD_ROWDIFF ? launch_voxel_B_slab<B_ZC_SLAB, 8, 4, true>(g, ypad, x, stop, st)
-                                    : launch_voxel_B_slab<B_ZC_SLAB, 8, 4, false>(g, ypad, x, stop, st);
-    if (g.sino_bf16 && g.nz >= B_ZC_2PASS)
-        return launch_voxel_B_2pass<B_ZC_2PASS, true>(g, ypad, x, stop, st);
-    return launch_voxel_B_z<B_ZC, B_PA>(g, ypad, x, stop, st, form);
+    if (g.sino_bf16) return launch_voxel_B_slab<B_ZC_SLAB, 8, 4, true, false>(g, ypad, x, stop, st);
+    return form == QUAD_ROWDIFF ? launch_voxel_B_slab<B_ZC_SLAB, 8, 4, false, true>(g, ypad, x, stop, st)
+                                : launch_voxel_B_slab<B_ZC_SLAB, 8, 4, false, false>(g, ypad, x, stop, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -32,19 +32,16 @@ constexpr int PAD_V = 2;   // rows, above and below each view
 constexpr int A_VR = CT_A_VR;
 constexpr int AT_VR = CT_AT_VR;
 constexpr int A_VR_MAX = A_VR > AT_VR ? A_VR : AT_VR;
-// consecutive z slices per back-projector thread: B_ZC for voxel_B_kernel,
-// B_ZC_SLAB for the 3D FP32 kernel, B_ZC_2PASS for the two-pass kernel on
-// bf16 quads.  The last run of a
-// column may pass nz: those slices are computed and discarded, and the
-// padded sinogram's row margin covers them too (sized for B_ZC_RUN_MAX).
+// consecutive z slices per thread: B_ZC_SLAB for the 3D back-projector
+// (voxel_B_slab_kernel), B_ZC for its transpose.  The last run of a column
+// may pass nz: those slices are computed and discarded, and the padded
+// sinogram's row margin covers them too (sized for B_ZC_RUN_MAX).
 #ifndef CT_B_ZC
 #define CT_B_ZC 8
 #endif
 constexpr int B_ZC = CT_B_ZC;
-constexpr int B_ZC_2PASS = 16;
-constexpr int B_ZC_SLAB = 16;   // the 3D FP32 back-projector (voxel_B_slab_kernel)
-constexpr int B_ZC_RUN_MAX = B_ZC > B_ZC_2PASS ? (B_ZC > B_ZC_SLAB ? B_ZC : B_ZC_SLAB)
-                                               : (B_ZC_2PASS > B_ZC_SLAB ? B_ZC_2PASS : B_ZC_SLAB);
+constexpr int B_ZC_SLAB = 16;
+constexpr int B_ZC_RUN_MAX = B_ZC > B_ZC_SLAB ? B_ZC : B_ZC_SLAB;
 
 
 // Per-view constants of the projector, from which a ray's direction, its
