@@ -217,14 +217,15 @@ def aggregate_over_ranks(elapsed_s, iters, world, device=None):
 # profiles/.
 NCU_TRAFFIC = {
     # (kernel, storage, workload): (bytes per launch, source file,
-    # sha256 of that file followed by ct_internal.cuh at capture time; the
-    # joseph_A entries were re-keyed when only the back-projector's run-length
-    # constants in ct_internal.cuh changed, the projector's code being the
-    # captured one)
+    # sha256 of that file followed by ct_internal.cuh at capture time; both
+    # entries were re-keyed when the index checks of the checked build were
+    # added, which compile to nothing in this build, and when only the
+    # back-projector's run-length constants in ct_internal.cuh changed (the
+    # projector's entry))
     ("voxel_B", "f32", "cone_256"): (1217241088 + 80254976, "ct_backproject.cu",
-                                     "1e7f0cce6c58c4a60dc490d47046881cd796ea76a28f5d363ca8e428e3de0c59"),
+                                     "384a35a6bd44de229b321f5cbd817631e2351aae804d6a5c4c1b47d051a585a7"),
     ("joseph_A", "f32", "cone_256"): (404909312 + 137606400, "ct_project.cu",
-                                      "67b72fa70b4b907746b6c77a4867773c98cc4a0083a7e00339742b3674dde173"),
+                                      "5c2f00396fc9f57152003c9fe41bc70704f031310d02e29f091b5479e102d0fe"),
 }
 
 
@@ -234,9 +235,9 @@ NCU_TRAFFIC = {
 # at least 4 for B's 128-bit warp loads, 1 for A's 32-bit ones).  Keyed like NCU_TRAFFIC.
 NCU_L1 = {
     ("voxel_B", "f32", "cone_256"): ({"data_pipe_frac": 0.801, "passes_per_request": 5.34}, "ct_backproject.cu",
-                                     "1e7f0cce6c58c4a60dc490d47046881cd796ea76a28f5d363ca8e428e3de0c59"),
+                                     "384a35a6bd44de229b321f5cbd817631e2351aae804d6a5c4c1b47d051a585a7"),
     ("joseph_A", "f32", "cone_256"): ({"data_pipe_frac": 0.453, "passes_per_request": 1.38}, "ct_project.cu",
-                                      "67b72fa70b4b907746b6c77a4867773c98cc4a0083a7e00339742b3674dde173"),
+                                      "5c2f00396fc9f57152003c9fe41bc70704f031310d02e29f091b5479e102d0fe"),
 }
 
 

@@ -413,6 +413,37 @@ CT_API ct_status ct_fault_set(const char *spec);
  * calling thread's next call. */
 CT_API const char *ct_fault_get(void);
 
+/* Index checks (checked builds).  The library built with -DCT_CHECK_BOUNDS
+ * (libct_checked.so; libct.so is the regular build) tests, where each is
+ * used, the margins and invariants that ct_geom_create derives from the
+ * geometry and on which the gathers of A and B rely (no counterpart in the
+ * paper; they guard the layouts of Sec. III's operators):
+ *   site 1  A: a sample's two z rows lie inside the volume copy's zero border;
+ *   site 2  A: the rays of a detector column move up at most one z row from
+ *           ray to ray (the two-row window);
+ *   site 3  A^T: the same for its row sums;
+ *   site 4  B: a sample's quad row lies inside its view's padded rows (the
+ *           row margin padv);
+ *   site 5  B: a column's quad lies inside the padded row;
+ *   site 6  A_S, A_S^T: the running voxel offset is the traversed voxel's.
+ * A failed check redirects the access into range (it never leaves its
+ * buffer), so the call's results are wrong, and records the first failure on
+ * the geometry.  ct_bounds_checked() returns 1 in a checked build, 0 in the
+ * regular one, where the checks are compiled out. */
+CT_API int ct_bounds_checked(void);
+
+/* Takes the geometry's first failed-check record and clears it, after the
+ * device has finished all work (cudaDeviceSynchronize).  *record is 0 when
+ * no check failed (always in the regular build); otherwise
+ *   bits 56..63  the site (1..6 above),
+ *   bits 32..55  the view (sites 1-5) or z slice (site 6),
+ *   bits  0..31  the offending value as a signed 32-bit integer: the z row
+ *                (1), the row step (2, 3), the padded row (4) or column (5),
+ *                the offset from the ray's base (6).
+ * The record is per geometry, shared by all streams using it.  Returns
+ * CT_EINVAL for null arguments, CT_ECUDA when the copy fails. */
+CT_API ct_status ct_bounds_take(ct_geom *geom, unsigned long long *record);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 CT_API const char *ct_last_error(void);
 

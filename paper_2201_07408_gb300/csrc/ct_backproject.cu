@@ -394,13 +394,17 @@ template <int ZC, bool BF, bool DIFF>
 __device__ __forceinline__ void column_samples(const GeomDev &g, const void *__restrict__ ypad, const ColumnView &c,
                                                int s, int view_stride, int pitch, float (&r)[ZC])
 {
-    const size_t vbase = size_t(s) * view_stride + c.col;
+    int col = c.col;
+    if (!CT_IN_BOUNDS(g, unsigned(col) < unsigned(pitch), BS_B_COL, s, col)) col = 0;
+    const size_t vbase = size_t(s) * view_stride + col;
 #pragma unroll
     for (int k = 0; k < ZC; ++k) {
         const float fv = fmaf(float(k), c.gv, c.fv0);
         const float v0f = floorf(fv);
         const float wv = fv - v0f;
-        const float4 nb = load_quad<BF>(ypad, vbase + size_t((int(v0f) + g.padv) * pitch));
+        int row = int(v0f) + g.padv;
+        if (!CT_IN_BOUNDS(g, unsigned(row) < unsigned(g.nvp), BS_B_ROW, s, row)) row = 0;
+        const float4 nb = load_quad<BF>(ypad, vbase + size_t(row * pitch));
         if (DIFF) {
             const float e0 = fmaf(c.wu, nb.y, nb.x);
             const float e1 = fmaf(c.wu, nb.w, nb.z);
@@ -489,15 +493,17 @@ __global__ void __launch_bounds__(B_TILE *B_TILE) voxel_B_kernel(GeomDev g, cons
 // its row index and the row pitch in bytes (the entries' forms as in
 // column_samples).
 template <int ZC, bool BF, bool DIFF>
-__device__ __forceinline__ void column_samples_at(const char *__restrict__ pv, const ColumnView &c, int pitch_bytes,
-                                                  float (&r)[ZC])
+__device__ __forceinline__ void column_samples_at(const GeomDev &g, int s, const char *__restrict__ pv,
+                                                  const ColumnView &c, int pitch_bytes, float (&r)[ZC])
 {
 #pragma unroll
     for (int k = 0; k < ZC; ++k) {
         const float fv = fmaf(float(k), c.gv, c.fv0);
         const float v0f = floorf(fv);
         const float wv = fv - v0f;
-        const float4 nb = load_quad<BF>(pv + int(v0f) * pitch_bytes, 0);
+        int row = int(v0f);   // relative to the view's first detector row
+        if (!CT_IN_BOUNDS(g, unsigned(row + g.padv) < unsigned(g.nvp), BS_B_ROW, s, row + g.padv)) row = -g.padv;
+        const float4 nb = load_quad<BF>(pv + row * pitch_bytes, 0);
         if (DIFF) {
             const float e0 = fmaf(c.wu, nb.y, nb.x);
             const float e1 = fmaf(c.wu, nb.w, nb.z);
@@ -590,10 +596,12 @@ __global__ void __launch_bounds__(32 * TY, MINB) voxel_B_slab_kernel(GeomDev g, 
             const ColumnView c = column_view(g, sviews[2 * s], sviews[2 * s + 1], cx, cy, zfirst);
             if (c.skip) continue;
             constexpr int ENTRY = BF ? 8 : 16;   // bytes per quad entry
+            int col = c.col;
+            if (!CT_IN_BOUNDS(g, unsigned(col) < unsigned(pitch), BS_B_COL, s, col)) col = 0;
             const char *pv = static_cast<const char *>(ypad) +
-                             ENTRY * (size_t(s) * view_stride + size_t(g.padv) * pitch + c.col);
+                             ENTRY * (size_t(s) * view_stride + size_t(g.padv) * pitch + col);
             float r[ZC];
-            column_samples_at<ZC, BF, DIFF>(pv, c, ENTRY * pitch, r);
+            column_samples_at<ZC, BF, DIFF>(g, s, pv, c, ENTRY * pitch, r);
             accumulate<ZC, DIFF>(acc, r, c.w);
         }
         // x-lane sums belong to (X0 + tax, Y0 + tay), y-lane sums to (X0 + tbx, Y0 + tby)

@@ -122,4 +122,27 @@ const char *ct_fault_get(void)
     return copy.c_str();
 }
 
+int ct_bounds_checked(void)
+{
+#ifdef CT_CHECK_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+ct_status ct_bounds_take(ct_geom *geom, unsigned long long *record)
+{
+    if (!geom || !record) return set_error(CT_EINVAL, "ct_bounds_take: null argument");
+    *record = 0;
+#ifdef CT_CHECK_BOUNDS
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(record, geom->g.bounds_word, sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(geom->g.bounds_word, 0, sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_error(e, "ct_bounds_take");
+#endif
+    return CT_OK;
+}
+
 }  // extern "C"

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <vector>
@@ -152,6 +153,10 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         const double over = zslices * vx * mmax / d->dv_mm - 0.5 * (d->nv - 1);
         padv = std::max(PAD_V, int(std::ceil(std::max(over, 0.0))) + PAD_V);
     }
+#ifdef CT_CHECK_BOUNDS
+    // checked builds only: a margin may be imposed to exercise the row checks
+    if (const char *ev = std::getenv("CT_DEBUG_PADV")) padv = std::max(1, std::atoi(ev));
+#endif
     // 32-bit indexing of rays, voxels, padded copies and the padded sinogram
     const double lim = 2147483647.0;
     double nzp = d->nz + 2.0 * PAD_A;
@@ -244,6 +249,11 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         }
         k.a_window = (smin >= 0.0 && smax <= 0.98) ? 1 : 0;
     }
+#ifdef CT_CHECK_BOUNDS
+    // checked builds only: the projector may be told that no z clamp is
+    // needed, to exercise its z checks
+    if (std::getenv("CT_DEBUG_A_ZSAFE")) k.a_zsafe = 1;
+#endif
     // Ram-Lak taps of the ramp filter with the FBP scale folded in:
     // h[0] = 1/(4 tau^2), h[odd k] = -1/(pi^2 k^2 tau^2), h[even k] = 0, times tau * c_F.
     std::vector<float> taps(d->nu);
@@ -289,7 +299,11 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     size_t bT = Arena::align(taps.size() * sizeof(float));
     size_t bW = Arena::align(fft_tw.size() * sizeof(float2));
     size_t bH = Arena::align(fft_h.size() * sizeof(float));
-    cudaError_t e = cudaMalloc(&g->d_tables, bA + bB + bT + bW + bH);
+    size_t bWord = 0;
+#ifdef CT_CHECK_BOUNDS
+    bWord = Arena::align(sizeof(unsigned long long));
+#endif
+    cudaError_t e = cudaMalloc(&g->d_tables, bA + bB + bT + bW + bH + bWord);
     if (e != cudaSuccess) {
         delete g;
         return cuda_error(e, "cudaMalloc(geometry tables)");
@@ -315,6 +329,15 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     k.fft_n = fft_n;
     k.fft_tw = reinterpret_cast<const float2 *>(base + bA + bB + bT);
     k.fft_h = reinterpret_cast<const float *>(base + bA + bB + bT + bW);
+#ifdef CT_CHECK_BOUNDS
+    k.bounds_word = reinterpret_cast<unsigned long long *>(base + bA + bB + bT + bW + bH);
+    e = cudaMemset(k.bounds_word, 0, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaFree(g->d_tables);
+        delete g;
+        return cuda_error(e, "cudaMemset(bounds word)");
+    }
+#endif
     *out = g;
     return CT_OK;
 }

@@ -108,7 +108,47 @@ struct GeomDev {
     const float *fft_h;
     // projector: 0 Joseph, 1 line intersection (Siddon)
     int siddon;
+#ifdef CT_CHECK_BOUNDS
+    // checked builds: the first failed index check of any kernel on this
+    // geometry, as a BoundsSite record (see bounds_ok); 0 when none failed
+    unsigned long long *bounds_word;
+#endif
 };
+
+// Index checks of checked builds (compiled with -DCT_CHECK_BOUNDS, which
+// builds libct_checked.so).  The gathers of A and B and the transposes'
+// row windows rely on margins and invariants that ct_geom_create derives
+// from the geometry's extremes (the row margin padv, a_zsafe, a_window); a
+// checked build tests each of them where it is used.  A failed check records
+// (site, view or plane, index) in the geometry's bounds word (the first
+// failure wins) and the access is redirected into range, so it never leaves
+// its buffer; the results are then wrong and the host reads the record with
+// ct_bounds_take.  In regular builds CT_IN_BOUNDS is the constant true and
+// the kernels are unchanged.
+enum BoundsSite {
+    BS_NONE = 0,
+    BS_A_Z = 1,          // projector: a sample's two z rows inside the zero border
+    BS_A_WINDOW = 2,     // projector: consecutive rays of a column move up at most one z row
+    BS_AT_WINDOW = 3,    // projector transpose: the same for its row sums
+    BS_B_ROW = 4,        // back-projector: a sample's quad row inside the view's padded rows
+    BS_B_COL = 5,        // back-projector: a column's quad inside the padded row
+    BS_SIDDON_VOXEL = 6  // line-intersection projector: a traversed voxel inside the grid
+};
+#ifdef CT_CHECK_BOUNDS
+__device__ __forceinline__ bool bounds_ok(const GeomDev &g, bool ok, int site, int where, int index)
+{
+    if (!ok) {
+        const unsigned long long rec = (static_cast<unsigned long long>(site) << 56) |
+                                       (static_cast<unsigned long long>(where & 0xffffff) << 32) |
+                                       static_cast<unsigned int>(index);
+        atomicCAS(g.bounds_word, 0ull, rec);
+    }
+    return ok;
+}
+#define CT_IN_BOUNDS(g, cond, site, where, index) ::ct::bounds_ok((g), (cond), (site), (where), (index))
+#else
+#define CT_IN_BOUNDS(g, cond, site, where, index) true
+#endif
 
 // Layout of a sinogram buffer that an operator writes.
 struct SinoLayout {

@@ -303,7 +303,9 @@ __global__ void __launch_bounds__(A_BLOCK, BF ? kAMinBlocksBF : kAMinBlocks) jos
             const float fz = fmaf(float(i), dzr, fz0);
             const float z0f = floorf(fz);
             const float wz = fz - z0f;
-            const int z0 = ZCLAMP ? min(max(int(z0f), -PAD_A), zmax) : int(z0f);
+            int z0 = ZCLAMP ? min(max(int(z0f), -PAD_A), zmax) : int(z0f);
+            if (!ZCLAMP && !CT_IN_BOUNDS(g, z0 >= -PAD_A && z0 <= zmax + PAD_A - 2, BS_A_Z, s, z0)) z0 = -PAD_A;
+            if (WINDOW && i > 0) (void)CT_IN_BOUNDS(g, z0 == z_prev || z0 == z_prev + 1, BS_A_WINDOW, s, z0 - z_prev);
             const float *r = rowp + (z0 + 1) * zstride;
             const float hi = row_lerp<BF>(r, wb);
             float lo;
@@ -496,6 +498,7 @@ __global__ void __launch_bounds__(A_BLOCK) joseph_At_kernel(GeomDev g, const flo
                 acc_lo += c_lo;
                 acc_hi += c_hi;
             } else {   // z0 == zc + 1: row zc is complete
+                (void)CT_IN_BOUNDS(g, z0 == zc + 1, BS_AT_WINDOW, s, z0 - zc);
                 flush(zc, acc_lo);
                 zc = z0;
                 acc_lo = acc_hi + c_lo;

@@ -112,6 +112,9 @@ __device__ __forceinline__ void walk(const GeomDev &g, const RayWalk &w, int bas
     const int max_steps = g.nx + g.ny + g.nz + 3;
     for (int n = 0; n < max_steps; ++n) {
         const float dt = fminf(dx, fminf(dy, dz));
+        // checked builds: the running offset is the voxel's (ix, iy, iz stay in the grid)
+        if (!CT_IN_BOUNDS(g, off == base + ix + iy * ystride + iz * zstride, BS_SIDDON_VOXEL, iz, off - base))
+            off = base + ix + iy * ystride + iz * zstride;
         visit(off, fmaxf(dt, 0.0f));
         // the axis crossed first steps (ties go to x, then y); the others move
         // dt closer to their next crossing.  Selects instead of branches: the

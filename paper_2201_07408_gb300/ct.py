@@ -17,7 +17,10 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libct.so")
+# CT_LIB=checked selects the index-checked build (libct_checked.so, see
+# ct_bounds_checked in include/ct.h); the default is the regular build
+LIB_PATH = os.path.join(_HERE, "_build", "libct_checked.so" if os.environ.get("CT_LIB") == "checked"
+                        else "libct.so")
 
 CT_OK, CT_EINVAL, CT_ENOMEM, CT_ECUDA, CT_ENONFINITE, CT_ETIMEOUT, CT_BREAKDOWN_LUCKY = range(7)
 CT_PARALLEL_2D, CT_CONE_3D = 0, 1
@@ -87,6 +90,8 @@ SIGNATURES = {
     "ct_gmres_state_destroy": (None, [_vp]),
     "ct_fault_set": (_i, [ctypes.c_char_p]),
     "ct_fault_get": (ctypes.c_char_p, []),
+    "ct_bounds_checked": (_i, []),
+    "ct_bounds_take": (_i, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]),
     "ct_last_error": (ctypes.c_char_p, []),
     "ct_version": (ctypes.c_char_p, []),
 }
@@ -99,7 +104,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libct.so is not built (%s): run `python -c \"import __graft_entry__ as g; "
+            raise RuntimeError("%s is not built: run `python -c \"import __graft_entry__ as g; "
                                "g.build()\"` or `python paper_2201_07408_gb300/build.py`" % LIB_PATH)
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
@@ -535,6 +540,35 @@ def fault_set(spec):
 
 def fault_get() -> str:
     return lib().ct_fault_get().decode()
+
+
+BOUNDS_SITES = {1: "A z rows", 2: "A row window", 3: "A^T row window", 4: "B row", 5: "B column",
+                6: "Siddon voxel offset"}
+
+
+def bounds_checked() -> bool:
+    """True when the loaded library is the index-checked build."""
+    return bool(lib().ct_bounds_checked())
+
+
+def decode_bounds_record(rec: int):
+    """(site, view or slice, value) of a ct_bounds_take record, None for 0."""
+    if not rec:
+        return None
+    site = rec >> 56
+    where = (rec >> 32) & 0xFFFFFF
+    value = rec & 0xFFFFFFFF
+    if value >= 1 << 31:
+        value -= 1 << 32
+    return site, where, value
+
+
+def bounds_take(g):
+    """Takes and clears the geometry's first failed index check (checked
+    builds): None, or (site, view or slice, value) as decode_bounds_record."""
+    rec = ctypes.c_ulonglong(0)
+    _check("ct_bounds_take", lib().ct_bounds_take(g.handle, ctypes.byref(rec)))
+    return decode_bounds_record(int(rec.value))
 
 
 def version() -> str:

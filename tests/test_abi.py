@@ -113,3 +113,26 @@ def test_fault_spec_from_environment(libct, env, canon, warns):
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == canon
     assert ("ignoring CT_FAULT" in r.stderr) == warns
+
+
+def test_checked_build_exports_every_declared_symbol_and_reports_itself(libct):
+    from paper_2201_07408_gb300 import build
+    Lc = ctypes.CDLL(build.LIB_CHECKED)
+    missing = [n for n in sorted(declared_symbols()) if not hasattr(Lc, n)]
+    assert not missing, missing
+    assert Lc.ct_bounds_checked() == 1
+    assert ctypes.CDLL(build.LIB).ct_bounds_checked() == 0
+
+
+def test_bounds_take_rejects_null_arguments(libct):
+    L = libct.lib()
+    rec = ctypes.c_ulonglong(7)
+    assert L.ct_bounds_take(None, ctypes.byref(rec)) == libct.CT_EINVAL
+    assert b"ct_bounds_take" in L.ct_last_error()
+
+
+@pytest.mark.parametrize("site,where,value", [(4, 17, -3), (1, 359, 12), (6, 0, 2**31 - 1), (2, 2**24 - 1, -2**31)])
+def test_bounds_record_decoding(libct, site, where, value):
+    rec = (site << 56) | (where << 32) | (value & 0xFFFFFFFF)
+    assert libct.decode_bounds_record(rec) == (site, where, value)
+    assert libct.decode_bounds_record(0) is None
