@@ -122,9 +122,19 @@ PAR2D_ANISO = Geometry(name="par2d_aniso", kind=PARALLEL_2D, nx=37, ny=29, nz=1,
 # slices (the row margin must cover them), while 8-slice runs end at nz
 CONE_Z40 = _cone("cone_z40", 40, 3.0, 48, 66, 44, 4.5, ang0=0.15)
 
+# Degenerate scans: one voxel; one view; a one-row cone-beam detector; a
+# one-voxel-wide column of slices; a 2D scan with three detector bins.
+CONE_VOXEL1 = _cone("cone_voxel1", 1, 10.0, 3, 5, 5, 8.0, ang0=0.2)
+CONE_1VIEW = _cone("cone_1view", 0, 3.0, 1, 20, 14, 5.0, nxyz=(12, 10, 9), ang0=0.4)
+CONE_1ROW = _cone("cone_1row", 0, 2.0, 24, 30, 1, 2.5, nxyz=(16, 16, 6), dv=4.0)
+CONE_COLUMN = _cone("cone_column", 0, 2.0, 8, 6, 30, 3.0, nxyz=(1, 1, 24), ang0=0.1)
+PAR2D_3BIN = Geometry(name="par2d_3bin", kind=PARALLEL_2D, nx=9, ny=7, nz=1, vox=1.0,
+                      n_views=5, ang0=0.0, span=math.pi, nu=3, nv=1, du=4.0, dv=1.0)
+DEGENERATE = [CONE_VOXEL1, CONE_1VIEW, CONE_1ROW, CONE_COLUMN, PAR2D_3BIN]
+
 WORKLOADS = {g.name: g for g in (PAR2D_64, CONE_128, CONE_256, CONE_512, CONE_512_CUT64,
                                  CONE_GRAD32, CONE_SMALL, CONE_ANISO, CONE_THIN, PAR2D_ANISO,
-                                 CONE_Z40)}
+                                 CONE_Z40, *DEGENERATE)}
 
 
 def scaled(g: Geometry, **kw) -> Geometry:

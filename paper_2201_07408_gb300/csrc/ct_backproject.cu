@@ -283,8 +283,7 @@ static cudaError_t launch_ramp_fft(const GeomDev &g, const float *src, float *ds
 {
     const FftShape fs = fft_shape(g.fft_n);
     if (fs.smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(ramp_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(fs.smem));
+        cudaError_t e = raise_dyn_smem(reinterpret_cast<const void *>(ramp_fft_kernel), fs.smem);
         if (e != cudaSuccess) return e;
     }
     int per_sm = 0;
@@ -630,8 +629,7 @@ static cudaError_t launch_voxel_B_slab(const GeomDev &g, const float *ypad, floa
     dim3 block(32, TY);
     const size_t smem = size_t(g.n_views) * 2 * sizeof(float4) + size_t(ZC) * TY * (B_TILE + 1) * sizeof(float) +
                         size_t(g.n_views) * sizeof(short);
-    cudaError_t e = cudaFuncSetAttribute(voxel_B_slab_kernel<ZC, TY, MINB, BF, DIFF>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void *>(voxel_B_slab_kernel<ZC, TY, MINB, BF, DIFF>), smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.nx + 31) / 32, (g.ny + TY - 1) / TY, (g.nz + ZC - 1) / ZC);
     voxel_B_slab_kernel<ZC, TY, MINB, BF, DIFF><<<grid, block, smem, st>>>(g, ypad, x, stop);
@@ -644,8 +642,7 @@ static cudaError_t launch_voxel_B_t(const GeomDev &g, const float *ypad, float *
     dim3 block(B_TILE, B_TILE);
     const size_t smem = size_t(g.n_views) * 2 * sizeof(float4);
     if (smem > 8 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(voxel_B_kernel<ZC, BF, DIFF, PA>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        cudaError_t e = raise_dyn_smem(reinterpret_cast<const void *>(voxel_B_kernel<ZC, BF, DIFF, PA>), smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((g.nx + B_TILE - 1) / B_TILE, (g.ny + B_TILE - 1) / B_TILE, (g.nz + ZC - 1) / ZC);
@@ -796,11 +793,9 @@ template <int ZC, int MINB>
 static cudaError_t launch_voxel_Bt_slab(const GeomDev &g, const float *x, float *y, const int *stop, cudaStream_t st)
 {
     const size_t smem = size_t(g.n_views) * 2 * sizeof(float4);
-    cudaError_t e = cudaFuncSetAttribute(voxel_Bt_slab_kernel<ZC, true, MINB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void *>(voxel_Bt_slab_kernel<ZC, true, MINB>), smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(voxel_Bt_slab_kernel<ZC, false, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(smem));
+        e = raise_dyn_smem(reinterpret_cast<const void *>(voxel_Bt_slab_kernel<ZC, false, MINB>), smem);
     if (e != cudaSuccess) return e;
     dim3 block(32, 8);
     dim3 gx((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + ZC - 1) / ZC);

@@ -5,6 +5,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "ct_internal.cuh"
@@ -75,6 +78,21 @@ size_t plane_copies_bytes(const GeomDev &g)
 size_t padded_sino_bytes(const GeomDev &g)
 {
     return Arena::align(size_t(g.n_views) * g.nvp * g.pitchU * 4 * sizeof(float));
+}
+
+cudaError_t raise_dyn_smem(const void *func, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> limit;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = limit[{dev, func}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e == cudaSuccess) cur = bytes;
+    return e;
 }
 
 int num_sms()

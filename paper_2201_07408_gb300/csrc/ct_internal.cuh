@@ -330,6 +330,11 @@ cudaError_t launch_voxel_Bt(const GeomDev &g, const float *x, float *y, const in
 
 // --- vector kernels (ct_krylov.cu) ---------------------------------------------
 int num_sms();
+// Raises the dynamic shared-memory limit of kernel `func` on the current
+// device to at least `bytes` (never lowers it).  The limit is process-wide per
+// function, so callers on other threads with other sizes (geometries with
+// other view counts) must not lower it under a launch that needs more.
+cudaError_t raise_dyn_smem(const void *func, size_t bytes);
 
 // --- host-side fault injection (ct_fault.cu; CT_FAULT, ct_fault_set) --------------
 struct FaultSpec {

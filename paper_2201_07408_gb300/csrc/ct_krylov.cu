@@ -538,8 +538,8 @@ static cudaError_t combine_t(const TB *V, size_t ldv, int k, size_t len, const d
 {
     const size_t smem = std::max<size_t>(1, size_t(k)) * sizeof(float);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(combine_kernel<TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(std::min<size_t>(smem, 200 * 1024)));
+        cudaError_t e = raise_dyn_smem(reinterpret_cast<const void *>(combine_kernel<TB>),
+                                       std::min<size_t>(smem, 200 * 1024));
         if (e != cudaSuccess) return e;
     }
     const unsigned blocks = unsigned(std::max<size_t>(1, std::min((len + RED_BLOCK - 1) / RED_BLOCK,

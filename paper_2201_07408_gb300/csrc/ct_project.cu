@@ -55,6 +55,46 @@ __device__ __forceinline__ void clip_planes(float fc, float g, float lo, float h
     p1 = min(p1, int(floorf(th)));
 }
 
+// Planes on which some ray of a run of rays has its coordinate f inside
+// [lo, hi] (with clip_planes's half-voxel margin), the run's rays lying
+// between its first ray (fc_f, g_f) and its last (fc_l, g_l) on every plane
+// (f is linear in the ray's row, and the rows run in order).  On a plane the
+// run covers [min(f_f, f_l), max(f_f, f_l)], so the plane is needed when one
+// end ray is above lo and one end ray is below hi.  Each condition holds on a
+// union of two half-lines of planes; its hull is taken (exact when one end
+// ray stays above the other over the grid, as when the source lies outside
+// the grid's plane range; otherwise a superset, whose extra planes add
+// zeros).  Joining the two end rays' own plane ranges instead misses the far
+// planes of the rays between them when the end rays leave through opposite
+// faces (a short volume under a tall detector).
+__device__ __forceinline__ void clip_planes_run(float fc_f, float g_f, float fc_l, float g_l, float lo, float hi,
+                                                float ca, int Na, int &p0, int &p1)
+{
+    constexpr float BIG = 3.0e38f;
+    auto hull = [](int a0, int a1, int b0, int b1, int &h0, int &h1) {
+        if (a0 > a1) {
+            h0 = b0;
+            h1 = b1;
+        } else if (b0 > b1) {
+            h0 = a0;
+            h1 = a1;
+        } else {
+            h0 = min(a0, b0);
+            h1 = max(a1, b1);
+        }
+    };
+    int a0 = 0, a1 = Na - 1, b0 = 0, b1 = Na - 1, u0, u1, w0, w1;
+    clip_planes(fc_f, g_f, lo, BIG, ca, Na, a0, a1);   // first ray above lo
+    clip_planes(fc_l, g_l, lo, BIG, ca, Na, b0, b1);   // last ray above lo
+    hull(a0, a1, b0, b1, u0, u1);
+    a0 = 0, a1 = Na - 1, b0 = 0, b1 = Na - 1;
+    clip_planes(fc_f, g_f, -BIG, hi, ca, Na, a0, a1);  // first ray below hi
+    clip_planes(fc_l, g_l, -BIG, hi, ca, Na, b0, b1);  // last ray below hi
+    hull(a0, a1, b0, b1, w0, w1);
+    p0 = max(p0, max(u0, w0));
+    p1 = min(p1, min(u1, w1));
+}
+
 __device__ __forceinline__ RaySetup ray_setup(const GeomDev &g, int s, int iv, int iu)
 {
     const float4 *vp = reinterpret_cast<const float4 *>(g.viewA + s);
@@ -252,18 +292,13 @@ __global__ void __launch_bounds__(A_BLOCK, BF ? kAMinBlocksBF : kAMinBlocks) jos
     const float gz_step = g.dv * b.x * inv_da;           // d gz / d iv
     const float gz0 = (float(iv0) - g.cv) * gz_step;     // gz of the first ray
 
-    // plane range: the b range of the column joined with the z ranges of its
-    // first and last ray, then joined over the warp
+    // plane range: the b range of the column met with the planes on which
+    // any of its rays is inside the grid in z, then joined over the warp
     int p0 = 0, p1 = Na - 1;
     clip_planes(fbc, gb, -1.0f, float(Nb), ca, Na, p0, p1);
     {
         const float gzl = (float(ivl) - g.cv) * gz_step;
-        int q0 = 0, q1 = Na - 1, r0 = 0, r1 = Na - 1;
-        clip_planes(fmaf(-Sv, gz0, g.cz), gz0, -1.0f, float(g.nz), ca, Na, q0, q1);
-        clip_planes(fmaf(-Sv, gzl, g.cz), gzl, -1.0f, float(g.nz), ca, Na, r0, r1);
-        const int z0 = min(q0, r0), z1 = max(q1, r1);
-        p0 = max(p0, z0);
-        p1 = min(p1, z1);
+        clip_planes_run(fmaf(-Sv, gz0, g.cz), gz0, fmaf(-Sv, gzl, g.cz), gzl, -1.0f, float(g.nz), ca, Na, p0, p1);
     }
     if (!live) {  // idle lanes do not widen the warp's range
         p0 = Na;
@@ -439,11 +474,7 @@ __global__ void __launch_bounds__(A_BLOCK) joseph_At_kernel(GeomDev g, const flo
     clip_planes(fbc, gb, -1.0f, float(Nb), ca, Na, p0, p1);
     {
         const float gzl = (float(ivl) - g.cv) * gz_step;
-        int q0 = 0, q1 = Na - 1, r0 = 0, r1 = Na - 1;
-        clip_planes(fmaf(-Sv, gz0, g.cz), gz0, -1.0f, float(g.nz), ca, Na, q0, q1);
-        clip_planes(fmaf(-Sv, gzl, g.cz), gzl, -1.0f, float(g.nz), ca, Na, r0, r1);
-        p0 = max(p0, min(q0, r0));
-        p1 = min(p1, max(q1, r1));
+        clip_planes_run(fmaf(-Sv, gz0, g.cz), gz0, fmaf(-Sv, gzl, g.cz), gzl, -1.0f, float(g.nz), ca, Na, p0, p1);
     }
     if (!any) {   // nothing to add: this thread's rays do not widen the warp's range
         p0 = Na;

@@ -3,7 +3,7 @@
 record each call left on its geometry.  Called by tests/test_gpu_checked.py
 in a child process, so that the checked library is the only one loaded.
 
-    python tests/checked_run.py all       every operator and solver on the small scans
+    python tests/checked_run.py all       every operator and solver on the small and degenerate scans
     python tests/checked_run.py margin    B_un on cone_small (run with CT_DEBUG_PADV set)
     python tests/checked_run.py zsafe     A on a tall-detector scan (run with CT_DEBUG_A_ZSAFE set)
 
@@ -66,7 +66,7 @@ def solvers(g, spec, y, out):
 
 def run_all():
     res = {}
-    specs = [ci.CONE_SMALL, ci.CONE_ANISO, ci.CONE_THIN, ci.CONE_Z40, ci.PAR2D_ANISO, TALL]
+    specs = [ci.CONE_SMALL, ci.CONE_ANISO, ci.CONE_THIN, ci.CONE_Z40, ci.PAR2D_ANISO, TALL] + ci.DEGENERATE
     for spec in specs:
         for storage, projector in (("f32", "joseph"), ("bf16", "joseph"), ("f32", "siddon")):
             if projector == "siddon" and spec.kind != ci.CONE_3D:

@@ -1,9 +1,9 @@
 """The index-checked build (libct_checked.so) on the GPU.
 
-Every operator and solver on the small scans (FP32 and BF16 storage, both
-projectors) must leave no failed check: the row margin of the back-projector,
-the projector's z border and row window, and the line-intersection walk's
-voxel offsets hold on every sample.  Then each check is shown to fire when
+Every operator and solver on the small and degenerate scans (FP32 and BF16
+storage, both projectors) must leave no failed check: the row margin of the
+back-projector, the projector's z border and row window, and the
+line-intersection walk's voxel offsets hold on every sample.  Then each check is shown to fire when
 its precondition is removed on the host, in the checked build only:
 
 * CT_DEBUG_PADV=2 shrinks the back-projector's row margin on cone_small
@@ -48,7 +48,7 @@ def run(mode, **env):
 
 def test_no_check_fails_on_any_operator_or_solver():
     res = run("all")
-    assert len(res) == 17
+    assert len(res) == 31
     failed = {case: [(name, rec) for name, rec in calls if rec is not None] for case, calls in res.items()}
     failed = {k: v for k, v in failed.items() if v}
     assert not failed, failed

@@ -107,3 +107,35 @@ def test_concurrent_operator_calls_equal_sequential_ones(ct):
     run_threads([lambda i=i: work(i) for i in range(len(xs))])
     for (y, v), (y0, v0) in zip(out, ref):
         assert torch.equal(y, y0) and torch.equal(v, v0)
+
+
+def test_concurrent_operators_on_geometries_of_different_view_counts(ct):
+    """The back-projector's shared memory grows with the view count, and a
+    kernel's shared-memory limit is process-wide: threads running the same
+    kernels on geometries with 60, 45 and 36 views (each on its own stream)
+    must all launch, and give what the same calls give alone."""
+    specs = [ci.CONE_SMALL, ci.CONE_ANISO, ci.CONE_THIN, ci.CONE_SMALL, ci.CONE_ANISO, ci.CONE_THIN]
+    geoms = [ct.Geometry.from_spec(s) for s in specs]
+    ys = [data(ct, g, s, seed=30 + i) for i, (g, s) in enumerate(zip(geoms, specs))]
+    ref = [(ct.backproject_B(g, y, "fbp").clone(), ct.adjoint_Bt(g, ct.backproject_B(g, y), "un").clone())
+           for g, y in zip(geoms, ys)]
+    torch.cuda.synchronize()
+    out = [None] * len(specs)
+
+    def work(i):
+        g, y, spec = geoms[i], ys[i], specs[i]
+        st = torch.cuda.Stream()
+        v = torch.empty(spec.vol_shape, device="cuda")
+        w = torch.empty(spec.sino_shape, device="cuda")
+        for _ in range(20):
+            ct.ct_backproject_B(g, y, v, "fbp", stream=st)
+        u = torch.empty(spec.vol_shape, device="cuda")
+        ct.ct_backproject_B(g, y, u, "un", stream=st)
+        ct.ct_adjoint_Bt(g, u, w, "un", stream=st)
+        st.synchronize()
+        out[i] = (v, w)
+    run_threads([lambda i=i: work(i) for i in range(len(specs))])
+    for (v, w), (v0, w0) in zip(out, ref):
+        assert torch.equal(v, v0)
+        # B^T accumulates with FP32 atomics: equal up to summation order
+        assert float((w - w0).norm() / w0.norm()) <= 1e-6

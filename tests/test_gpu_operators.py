@@ -273,3 +273,26 @@ def test_siddon_gpu_dot_product(ct):
     lhs = float((ax * y.double()).sum())
     rhs = float((x.double() * ct.adjoint_At(g, y).double()).sum())
     assert abs(lhs - rhs) <= 1e-5 * float(ax.norm() * y.double().norm())
+
+
+@pytest.mark.parametrize("spec", ci.DEGENERATE, ids=lambda s: s.name)
+def test_degenerate_scans_match_oracle(ct, spec):
+    """One voxel, one view, a one-row cone-beam detector, a one-voxel-wide
+    column, three detector bins: every operator against the oracle over its
+    whole output (tiles far larger than the grid, z runs past nz, lanes past
+    nu and nv)."""
+    g = ct.Geometry.from_spec(spec)
+    x = ci.random_vector(spec.n, seed=71, positive=True).astype(np.float32).reshape(spec.vol_shape)
+    y = ci.random_vector(spec.m, seed=72, positive=True).astype(np.float32).reshape(spec.sino_shape)
+    x64, y64 = x.astype(np.float64), y.astype(np.float64)
+    checks = [
+        ("A", host(ct.project_A(g, dev(x))), oracle.project_A(spec, x64)),
+        ("B_un", host(ct.backproject_B(g, dev(y), "un")), oracle.backproject_B(spec, y64)),
+        ("B_fbp", host(ct.backproject_B(g, dev(y), "fbp")), oracle.backproject_B(spec, y64, filtered=True)),
+        ("F", host(ct.ramp_F(g, dev(y))), oracle.ramp_F(spec, y64)),
+        ("At", host(ct.adjoint_At(g, dev(y))), oracle.adjoint_At(spec, y64)),
+        ("Bt_un", host(ct.adjoint_Bt(g, dev(x), "un")), oracle.adjoint_Bt(spec, x64, filtered=False)),
+        ("Bt_fbp", host(ct.adjoint_Bt(g, dev(x), "fbp")), oracle.adjoint_Bt(spec, x64, filtered=True)),
+    ]
+    for name, out, ref in checks:
+        assert rel(out, ref) <= OP_TOL, (name, rel(out, ref))

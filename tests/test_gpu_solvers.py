@@ -459,3 +459,32 @@ def test_bagmres_with_siddon_projector_matches_oracle(ct, parity_log, spec, b_ki
         rr = ct.ct_bagmres_solve(g, dev(b), k, xx, ct.make_opts(b_kind=b_kind, **o))
         return host(xx), rr.resid
     sens.check(parity_log, k, host(x), res.resid, rerun, solver="ba_siddon", case=spec.name, b_kind=b_kind)
+
+
+@pytest.mark.parametrize("spec,b_kind,k", [(ci.CONE_1VIEW, "un", 6), (ci.CONE_1ROW, "fbp", 6),
+                                          (ci.CONE_COLUMN, "un", 5), (ci.PAR2D_3BIN, "un", 4)],
+                         ids=lambda v: getattr(v, "name", str(v)))
+def test_bagmres_on_degenerate_scans_matches_oracle(ct, parity_log, spec, b_kind, k):
+    """BA-GMRES (Eq. 5) on the degenerate scans against the oracle."""
+    b = ci.random_vector(spec.m, seed=73, positive=True).astype(np.float32)
+    g = ct.Geometry.from_spec(spec)
+    x, res = ct.bagmres(g, dev(b.reshape(spec.sino_shape)), k, b_kind=b_kind)
+    sens = oracle_with_sensitivity(krylov.ba_gmres, spec, b_kind, b, k, keep_basis=False)
+    assert res.status in (ct.CT_OK, ct.CT_BREAKDOWN_LUCKY)
+    assert res.iters == len(sens.ref["resid"]) - 1
+    sens.check(parity_log, k, host(x), res.resid[:res.iters + 1], case=spec.name, b_kind=b_kind)
+
+
+def test_one_voxel_scan_breaks_down_after_one_iteration(ct):
+    """n = 1: the Krylov space of BA is one-dimensional, so the first
+    iteration solves the least-squares problem exactly and reports a lucky
+    breakdown; x equals the oracle's (B b) / (B A e) for the single voxel."""
+    spec = ci.CONE_VOXEL1
+    b = ci.random_vector(spec.m, seed=74, positive=True).astype(np.float32)
+    g = ct.Geometry.from_spec(spec)
+    x, res = ct.bagmres(g, dev(b.reshape(spec.sino_shape)), 3)
+    assert res.status == ct.CT_BREAKDOWN_LUCKY and res.iters == 1
+    ops = oracle.Operators(spec, "un")
+    bb = float(ops.B(b.astype(np.float64))[0])
+    ba = float(ops.B(ops.A(np.ones(1)))[0])
+    assert abs(float(host(x)[0, 0, 0]) - bb / ba) <= 1e-5 * abs(bb / ba)
