@@ -217,15 +217,11 @@ def aggregate_over_ranks(elapsed_s, iters, world, device=None):
 # profiles/.
 NCU_TRAFFIC = {
     # (kernel, storage, workload): (bytes per launch, source file,
-    # sha256 of that file followed by ct_internal.cuh at capture time; both
-    # entries were re-keyed when the index checks of the checked build were
-    # added, which compile to nothing in this build, and when only the
-    # back-projector's run-length constants in ct_internal.cuh changed (the
-    # projector's entry))
-    ("voxel_B", "f32", "cone_256"): (1217241088 + 80254976, "ct_backproject.cu",
-                                     "384a35a6bd44de229b321f5cbd817631e2351aae804d6a5c4c1b47d051a585a7"),
-    ("joseph_A", "f32", "cone_256"): (404909312 + 137606400, "ct_project.cu",
-                                      "5c2f00396fc9f57152003c9fe41bc70704f031310d02e29f091b5479e102d0fe"),
+    # sha256 of that file followed by ct_internal.cuh at capture time)
+    ("voxel_B", "f32", "cone_256"): (1211157504 + 80132096, "ct_backproject.cu",
+                                     "ac84394ba345b871dd74aedc2a9bb7e62298ef996fbeae6641737b7e64229022"),
+    ("joseph_A", "f32", "cone_256"): (412163840 + 137549056, "ct_project.cu",
+                                      "c1b67033553caa0d83c0276ba58e3401460016ca6414d40ef57dac26541c49f8"),
 }
 
 
@@ -234,10 +230,10 @@ NCU_TRAFFIC = {
 # (l1tex__data_pipe_lsu_wavefronts_mem_lgds / l1tex__t_requests_pipe_lsu_mem_global_op_ld:
 # at least 4 for B's 128-bit warp loads, 1 for A's 32-bit ones).  Keyed like NCU_TRAFFIC.
 NCU_L1 = {
-    ("voxel_B", "f32", "cone_256"): ({"data_pipe_frac": 0.801, "passes_per_request": 5.34}, "ct_backproject.cu",
-                                     "384a35a6bd44de229b321f5cbd817631e2351aae804d6a5c4c1b47d051a585a7"),
-    ("joseph_A", "f32", "cone_256"): ({"data_pipe_frac": 0.453, "passes_per_request": 1.38}, "ct_project.cu",
-                                      "5c2f00396fc9f57152003c9fe41bc70704f031310d02e29f091b5479e102d0fe"),
+    ("voxel_B", "f32", "cone_256"): ({"data_pipe_frac": 0.797, "passes_per_request": 5.34}, "ct_backproject.cu",
+                                     "ac84394ba345b871dd74aedc2a9bb7e62298ef996fbeae6641737b7e64229022"),
+    ("joseph_A", "f32", "cone_256"): ({"data_pipe_frac": 0.452, "passes_per_request": 1.39}, "ct_project.cu",
+                                      "c1b67033553caa0d83c0276ba58e3401460016ca6414d40ef57dac26541c49f8"),
 }
 
 
