@@ -59,7 +59,8 @@ def test_round_bf16_helper():
     np.testing.assert_array_equal(got, t)
 
 
-@pytest.mark.parametrize("spec", [ci.CONE_SMALL, ci.CONE_ANISO, ci.PAR2D_ANISO], ids=lambda s: s.name)
+@pytest.mark.parametrize("spec", [ci.CONE_SMALL, ci.CONE_ANISO, ci.PAR2D_ANISO] + ci.DEGENERATE,
+                         ids=lambda s: s.name)
 def test_project_A_bf16_volume(ct, spec):
     g = ct.Geometry.from_spec(spec, vol_dtype="bf16")
     x = ci.phantom(spec)[0] + ci.random_vector(spec.n, 3, dtype=np.float32, positive=True).reshape(spec.vol_shape) * 1e-3
@@ -68,7 +69,10 @@ def test_project_A_bf16_volume(ct, spec):
     assert rel(y.cpu().numpy(), ref) <= 1e-5
 
 
-@pytest.mark.parametrize("spec", [ci.CONE_SMALL, ci.CONE_ANISO, ci.CONE_Z40, ci.PAR2D_ANISO], ids=lambda s: s.name)
+# cone_thin (5 slices) and the degenerate scans run the 3D back-projector's
+# 16-slice runs far past nz on bf16 quads
+@pytest.mark.parametrize("spec", [ci.CONE_SMALL, ci.CONE_ANISO, ci.CONE_Z40, ci.CONE_THIN, ci.PAR2D_ANISO]
+                         + ci.DEGENERATE, ids=lambda s: s.name)
 @pytest.mark.parametrize("b_kind", ["un", "fbp"])
 def test_backproject_B_bf16_sinogram(ct, spec, b_kind):
     g = ct.Geometry.from_spec(spec, sino_dtype="bf16")

@@ -296,3 +296,19 @@ def test_degenerate_scans_match_oracle(ct, spec):
     ]
     for name, out, ref in checks:
         assert rel(out, ref) <= OP_TOL, (name, rel(out, ref))
+
+
+@pytest.mark.parametrize("spec", [s for s in ci.DEGENERATE if s.kind == ci.CONE_3D], ids=lambda s: s.name)
+def test_siddon_on_degenerate_scans_matches_oracle(ct, spec):
+    """The line-intersection projector and its transpose on the degenerate
+    cone-beam scans (a one-voxel grid, one view, one detector row, a
+    one-voxel column)."""
+    g = ct.Geometry.from_spec(spec, projector="siddon")
+    x = ci.random_vector(spec.n, seed=75, positive=True).astype(np.float32).reshape(spec.vol_shape)
+    y = ci.random_vector(spec.m, seed=76, positive=True).astype(np.float32).reshape(spec.sino_shape)
+    out = host(ct.project_A(g, dev(x)))
+    ref = oracle.project_S(spec, x.astype(np.float64))
+    assert rel(out, ref) <= OP_TOL, rel(out, ref)
+    back = host(ct.adjoint_At(g, dev(y)))
+    ref_t = oracle.adjoint_St(spec, y.astype(np.float64))
+    assert rel(back, ref_t) <= SIDDON_T_TOL, rel(back, ref_t)
