@@ -132,6 +132,37 @@ PAR2D_3BIN = Geometry(name="par2d_3bin", kind=PARALLEL_2D, nx=9, ny=7, nz=1, vox
                       n_views=5, ang0=0.0, span=math.pi, nu=3, nv=1, du=4.0, dv=1.0)
 DEGENERATE = [CONE_VOXEL1, CONE_1VIEW, CONE_1ROW, CONE_COLUMN, PAR2D_3BIN]
 
+def random_geometry(seed: int) -> Geometry:
+    """A seeded random small scan within the library's limits, for parity
+    sweeps over shapes the named scans do not cover: grids of 1..40 voxels
+    per axis, 1..70 views over a span of 0.3..2 pi from any start angle,
+    source distances of 100..800 mm with magnification 1.1..3, detectors
+    covering 0.5..1.6 of the volume's shadow with pixel aspect 0.6..1.6;
+    every fifth one is a 2D parallel-beam scan."""
+    rng = np.random.default_rng(1000 + seed)
+    nx, ny = (int(v) for v in rng.integers(1, 41, size=2))
+    vox = float(rng.uniform(0.5, 4.0))
+    n_views = int(rng.integers(1, 71))
+    span = float(2 * math.pi if rng.random() < 0.5 else rng.uniform(0.3, 2 * math.pi))
+    ang0 = float(rng.uniform(0.0, 2 * math.pi))
+    half = 0.5 * vox * math.hypot(nx, ny)
+    if seed % 5 == 4:
+        nu = int(rng.integers(3, 97))
+        du = float(2 * half * rng.uniform(0.5, 1.6) / nu)
+        return Geometry(name="random%d" % seed, kind=PARALLEL_2D, nx=nx, ny=ny, nz=1, vox=vox,
+                        n_views=n_views, ang0=ang0, span=span, nu=nu, nv=1, du=du, dv=1.0)
+    nz = int(rng.integers(1, 41))
+    sod = float(max(rng.uniform(100.0, 800.0), 1.5 * half + 10.0))
+    sdd = float(sod * rng.uniform(1.1, 3.0))
+    mag = sdd / sod
+    nu = int(rng.integers(3, 97))
+    nv = int(rng.integers(1, 65))
+    du = float(2 * half * mag * rng.uniform(0.5, 1.6) / nu)
+    dv = float(du * rng.uniform(0.6, 1.6))
+    return Geometry(name="random%d" % seed, kind=CONE_3D, nx=nx, ny=ny, nz=nz, vox=vox, n_views=n_views,
+                    ang0=ang0, span=span, nu=nu, nv=nv, du=du, dv=dv, sod=sod, sdd=sdd)
+
+
 WORKLOADS = {g.name: g for g in (PAR2D_64, CONE_128, CONE_256, CONE_512, CONE_512_CUT64,
                                  CONE_GRAD32, CONE_SMALL, CONE_ANISO, CONE_THIN, PAR2D_ANISO,
                                  CONE_Z40, *DEGENERATE)}

@@ -4,6 +4,7 @@ record each call left on its geometry.  Called by tests/test_gpu_checked.py
 in a child process, so that the checked library is the only one loaded.
 
     python tests/checked_run.py all       every operator and solver on the small and degenerate scans
+    python tests/checked_run.py random    every operator on the seeded random scans
     python tests/checked_run.py margin    B_un on cone_small (run with CT_DEBUG_PADV set)
     python tests/checked_run.py zsafe     A on a tall-detector scan (run with CT_DEBUG_A_ZSAFE set)
 
@@ -28,6 +29,7 @@ from paper_2201_07408_gb300 import ct  # noqa: E402
 # a scan whose detector rows reach far above and below the 8-slice volume:
 # the projector's z rows leave the zero border, so it must clamp (a_zsafe 0)
 TALL = ci._cone("tall_detector", 0, 2.0, 30, 48, 40, 3.0, nxyz=(32, 32, 8))
+RANDOM_SCANS = 24   # ct_inputs.random_geometry(0..23)
 
 
 def operators(g, spec, out):
@@ -81,6 +83,25 @@ def run_all():
     return res
 
 
+def run_random(count):
+    """Every operator (FP32, BF16, line intersection) on seeded random scans."""
+    res = {}
+    for seed in range(count):
+        spec = ci.random_geometry(seed)
+        for storage, projector in (("f32", "joseph"), ("bf16", "joseph"), ("f32", "siddon")):
+            if projector == "siddon" and spec.kind != ci.CONE_3D:
+                continue
+            out = []
+            g = ct.Geometry.from_spec(spec, vol_dtype=storage, sino_dtype=storage, projector=projector)
+            y = operators(g, spec, out)
+            if storage == "f32" and projector == "joseph":
+                ct.bagmres(g, y, 4, b_kind="fbp")
+                out.append(("ba_fbp", ct.bounds_take(g)))
+            g.close()
+            res["%s/%s/%s" % (spec.name, storage, projector)] = out
+    return res
+
+
 def run_one(spec, what):
     g = ct.Geometry.from_spec(spec)
     x = torch.from_numpy(ci.phantom(spec)[0]).cuda()
@@ -99,6 +120,8 @@ def main():
         res = run_all()
     elif mode == "margin":
         res = run_one(ci.CONE_SMALL, "margin")
+    elif mode == "random":
+        res = run_random(int(sys.argv[2]) if len(sys.argv) > 2 else RANDOM_SCANS)
     elif mode == "zsafe":
         res = run_one(TALL, "zsafe")
     else:

@@ -54,6 +54,13 @@ def test_no_check_fails_on_any_operator_or_solver():
     assert not failed, failed
 
 
+def test_no_check_fails_on_random_scans():
+    res = run("random")
+    failed = {case: [(name, rec) for name, rec in calls if rec is not None] for case, calls in res.items()}
+    failed = {k: v for k, v in failed.items() if v}
+    assert len(res) > 40 and not failed, failed
+
+
 def test_row_check_fires_when_the_margin_is_too_small():
     res = run("margin", CT_DEBUG_PADV="2")
     assert res["A"] is None

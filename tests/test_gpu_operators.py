@@ -312,3 +312,31 @@ def test_siddon_on_degenerate_scans_matches_oracle(ct, spec):
     back = host(ct.adjoint_At(g, dev(y)))
     ref_t = oracle.adjoint_St(spec, y.astype(np.float64))
     assert rel(back, ref_t) <= SIDDON_T_TOL, rel(back, ref_t)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_scans_match_oracle(ct, seed):
+    """Seeded random small scans (ct_inputs.random_geometry: grid, views,
+    short and full spans, start angle, magnification, detector coverage and
+    pixel aspect all drawn): every operator of both projectors against the
+    oracle over its whole output."""
+    spec = ci.random_geometry(seed)
+    g = ct.Geometry.from_spec(spec)
+    x = ci.random_vector(spec.n, seed=77, positive=True).astype(np.float32).reshape(spec.vol_shape)
+    y = ci.random_vector(spec.m, seed=78, positive=True).astype(np.float32).reshape(spec.sino_shape)
+    x64, y64 = x.astype(np.float64), y.astype(np.float64)
+    checks = [
+        ("A", host(ct.project_A(g, dev(x))), oracle.project_A(spec, x64), OP_TOL),
+        ("B_un", host(ct.backproject_B(g, dev(y), "un")), oracle.backproject_B(spec, y64), OP_TOL),
+        ("B_fbp", host(ct.backproject_B(g, dev(y), "fbp")), oracle.backproject_B(spec, y64, filtered=True), OP_TOL),
+        ("F", host(ct.ramp_F(g, dev(y))), oracle.ramp_F(spec, y64), OP_TOL),
+        ("At", host(ct.adjoint_At(g, dev(y))), oracle.adjoint_At(spec, y64), OP_TOL),
+        ("Bt_un", host(ct.adjoint_Bt(g, dev(x), "un")), oracle.adjoint_Bt(spec, x64, filtered=False), OP_TOL),
+        ("Bt_fbp", host(ct.adjoint_Bt(g, dev(x), "fbp")), oracle.adjoint_Bt(spec, x64, filtered=True), OP_TOL),
+    ]
+    if spec.kind == ci.CONE_3D:
+        gs = ct.Geometry.from_spec(spec, projector="siddon")
+        checks += [("A_S", host(ct.project_A(gs, dev(x))), oracle.project_S(spec, x64), OP_TOL),
+                   ("A_S^T", host(ct.adjoint_At(gs, dev(y))), oracle.adjoint_St(spec, y64), SIDDON_T_TOL)]
+    for name, out, ref, tol in checks:
+        assert rel(out, ref) <= tol, (spec, name, rel(out, ref))
