@@ -87,7 +87,10 @@ def gmres_core(S, r0, k, keep_basis=True):
         R[:j + 2, j] = col
         g[j + 1] = -sn[j] * g[j]
         g[j] = cs[j] * g[j]
-        resid.append(abs(g[j + 1]))
+        # the least-squares residual is |g[j+1]| while R[j, j] != 0; a column
+        # that vanishes after the rotations (only on breakdown: S is singular
+        # on the invariant space) cannot reduce g[j], which then stays
+        resid.append(abs(g[j + 1]) if rjj != 0.0 else math.hypot(g[j], g[j + 1]))
         iters = j + 1
         if breakdown:
             break
@@ -102,10 +105,13 @@ def gmres_core(S, r0, k, keep_basis=True):
 
 
 def _back_substitute(R, g):
+    """y = R^{-1} g for upper-triangular R; a zero diagonal entry (the
+    vanished column of a singular breakdown) gets y[i] = 0, the minimum-norm
+    least-squares choice."""
     k = R.shape[0]
     y = np.zeros(k)
     for i in range(k - 1, -1, -1):
-        y[i] = (g[i] - R[i, i + 1:] @ y[i + 1:]) / R[i, i]
+        y[i] = (g[i] - R[i, i + 1:] @ y[i + 1:]) / R[i, i] if R[i, i] != 0.0 else 0.0
     return y
 
 

@@ -9,7 +9,8 @@ B = A^T; with an unmatched pair it can diverge (Sec. III, Fig. 2).  Pins:
   * residual history non-increasing and equal to the recomputed residual;
   * iterates equal the least-squares minimiser over an explicitly built
     Krylov basis (dense, tiny), and at k = n the direct solve of BAx = Bb;
-  * lucky breakdown on an invariant subspace returns the exact solution;
+  * lucky breakdown on an invariant subspace returns the exact solution, and
+    on a subspace where the operator is singular the least-squares residual;
   * BA-GMRES iterates do not depend on the scale of B;
   * matched CGLS equals the Krylov least-squares minimiser; unmatched CGLS
     reaches a minimum data residual and then diverges, while BA-GMRES on the
@@ -132,6 +133,32 @@ def test_lucky_breakdown_gives_exact_solution():
     assert out["breakdown"] and out["iters"] == 3
     np.testing.assert_allclose(out["z"][-1], r0 / d, rtol=1e-12, atol=1e-14)
     assert out["resid"][-1] <= 1e-12
+
+
+def test_breakdown_on_a_singular_operator_keeps_the_least_squares_residual():
+    """When the Krylov space becomes invariant and the operator is singular
+    on it, the new Hessenberg column vanishes after the rotations: the
+    minimum of ||r0 - S z|| over the space is reached at the previous
+    iterate and stays above zero.  Brute force (dense least squares over the
+    explicit Krylov basis) fixes the history: S = 0 keeps ||r0||; S =
+    diag(1, 0) with r0 = (1, 1) gives sqrt 2, then 1 and 1 (S z = (z_1, 0)
+    never reaches the second component)."""
+    r0 = np.array([0.3, -1.2, 2.0])
+    out = krylov.gmres_core(lambda v: 0.0 * v, r0, 3)
+    assert out["breakdown"] and out["iters"] == 1
+    np.testing.assert_allclose(out["resid"], [np.linalg.norm(r0)] * 2, rtol=1e-15)
+    assert np.all(out["z"][-1] == 0.0)
+    S = np.diag([1.0, 0.0])
+    r0 = np.array([1.0, 1.0])
+    out = krylov.gmres_core(lambda v: S @ v, r0, 4)
+    assert out["breakdown"] and out["iters"] == 2
+    for j in (1, 2):
+        K = krylov_matrix(S, r0, j)
+        c = np.linalg.lstsq(S @ K, r0, rcond=None)[0]
+        assert abs(out["resid"][j] - np.linalg.norm(r0 - S @ K @ c)) <= 1e-12
+        np.testing.assert_allclose(S @ out["z"][j - 1], S @ K @ c, atol=1e-12)
+        assert np.all(np.isfinite(out["z"][j - 1]))
+    np.testing.assert_allclose(out["resid"], [math.sqrt(2.0), 1.0, 1.0], rtol=1e-12)
 
 
 def test_ba_gmres_iterates_independent_of_B_scale(tiny2d):
