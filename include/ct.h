@@ -58,7 +58,11 @@ typedef enum {
     CT_ENONFINITE = 4,      /* a norm became NaN/Inf during a solve */
     CT_ETIMEOUT = 5,        /* a bounded device wait gave up */
     CT_BREAKDOWN_LUCKY = 6  /* informational: the Krylov space became invariant;
-                               the returned solution is exact and valid */
+                               the returned iterate is valid: it minimises
+                               the residual over that space, which solves the
+                               system exactly unless the operator is singular
+                               on it (then resid_hist[iters_done] > 0 shows
+                               the residual that remains) */
 } ct_status;
 
 typedef enum { CT_PARALLEL_2D = 0, CT_CONE_3D = 1 } ct_geom_kind;
@@ -177,8 +181,8 @@ CT_API ct_status ct_ramp_F(const ct_geom *geom, const float *y_dev, float *yf_de
  *   opts:       NULL = defaults.
  *   iters_done: iterations performed (< k after a tolerance stop or a lucky
  *               breakdown).  May be NULL.
- * Returns CT_BREAKDOWN_LUCKY (solution valid) when the Krylov space became
- * invariant, CT_ENONFINITE when a norm was NaN/Inf. */
+ * Returns CT_BREAKDOWN_LUCKY (solution valid, see ct_status) when the Krylov
+ * space became invariant, CT_ENONFINITE when a norm was NaN/Inf. */
 CT_API ct_status ct_bagmres_solve(const ct_geom *geom, const float *b_dev, int k, float *x_out_dev,
                            double *resid_hist, const ct_solve_opts *opts, int *iters_done,
                            void *stream);

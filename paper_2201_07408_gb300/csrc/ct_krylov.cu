@@ -464,7 +464,10 @@ __global__ void givens_kernel(int j, int k, double *H, const double *H2, double 
     r[j + 1] = 0.0;
     g[j + 1] = -s * g[j];
     g[j] = c * g[j];
-    resid[j + 1] = fabs(g[j + 1]);
+    // a column that vanishes after the rotations (a breakdown on which the
+    // operator is singular) cannot reduce g[j]: the least-squares residual
+    // stays, and the back substitution gives that coefficient 0
+    resid[j + 1] = rr != 0.0 ? fabs(g[j + 1]) : hypot(g[j], g[j + 1]);
     st->iters = j + 1;
     if (lucky || rr == 0.0) {
         st->status = ST_LUCKY;

@@ -488,3 +488,53 @@ def test_one_voxel_scan_breaks_down_after_one_iteration(ct):
     bb = float(ops.B(b.astype(np.float64))[0])
     ba = float(ops.B(ops.A(np.ones(1)))[0])
     assert abs(float(host(x)[0, 0, 0]) - bb / ba) <= 1e-5 * abs(bb / ba)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4, 5, 7, 11])
+@pytest.mark.parametrize("solver", ["ba", "ab", "cgls"])
+def test_solvers_on_random_scans_match_oracle(ct, parity_log, seed, solver):
+    """BA-GMRES (Eq. 5), AB-GMRES (Eq. 4) and CGLS (Eqs. 2-3) on seeded
+    random small scans (ct_inputs.random_geometry), 6 iterations, B_FBP for
+    the GMRES solves and B_un for CGLS, against the oracle under the solver
+    bar."""
+    spec = ci.random_geometry(seed)
+    k = 6
+    b = ci.random_vector(spec.m, seed=79, positive=True).astype(np.float32)
+    g = ct.Geometry.from_spec(spec)
+    b_kind = "un" if solver == "cgls" else "fbp"
+    run = {"ba": ct.bagmres, "ab": ct.abgmres, "cgls": ct.cgls}[solver]
+    ref_solver = {"ba": krylov.ba_gmres, "ab": krylov.ab_gmres, "cgls": krylov.cgls}[solver]
+    x, res = run(g, dev(b.reshape(spec.sino_shape)), k, b_kind=b_kind)
+    kw = {} if solver == "cgls" else {"keep_basis": False}
+    sens = oracle_with_sensitivity(ref_solver, spec, b_kind, b, k, **kw)
+    n_ref = len(sens.ref["resid"]) - 1
+    assert res.iters == n_ref, (res.iters, n_ref)
+    if sens.ref["resid"][0] == 0.0:
+        # B b = 0 (every voxel centre of a thin-detector scan projects off the
+        # detector, so the voxel-driven B sees nothing): x = 0 at once
+        assert res.resid[0] == 0.0 and not host(x).any()
+        return
+
+    def rerun(**o):
+        xx, rr = run(g, dev(b.reshape(spec.sino_shape)), k, b_kind=b_kind, **o)
+        return host(xx), rr.resid[:n_ref + 1]
+    sens.check(parity_log, k, host(x), res.resid[:n_ref + 1], None if solver == "cgls" else rerun,
+               solver=solver, case=spec.name, b_kind=b_kind)
+
+
+def test_singular_breakdown_keeps_the_residual(ct):
+    """AB-GMRES on a scan whose voxel-driven B sees nothing (every voxel
+    centre of the 26 slices projects off the 13-row detector, so A B = 0):
+    the first iteration breaks down on a zero Hessenberg column, the
+    residual stays ||b|| (the oracle's least-squares residual) and x = 0."""
+    spec = ci.random_geometry(7)
+    b = ci.random_vector(spec.m, seed=79, positive=True).astype(np.float32)
+    g = ct.Geometry.from_spec(spec)
+    x, res = ct.abgmres(g, dev(b.reshape(spec.sino_shape)), 5, b_kind="fbp")
+    ops = oracle.Operators(spec, "fbp")
+    ref = krylov.ab_gmres(ops.A, ops.B, b.astype(np.float64), 5, keep_basis=False)
+    assert res.status == ct.CT_BREAKDOWN_LUCKY and res.iters == 1 == ref["iters"]
+    bn = float(np.linalg.norm(b.astype(np.float64)))
+    np.testing.assert_allclose(res.resid[:2], [bn, bn], rtol=1e-6)
+    np.testing.assert_allclose(ref["resid"], [bn, bn], rtol=1e-12)
+    assert not host(x).any()
