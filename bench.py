@@ -20,6 +20,7 @@ import argparse
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -211,17 +212,17 @@ def aggregate_over_ranks(elapsed_s, iters, world, device=None):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# one ncu capture of the kernel on the workload, with the SHA-256 of the
-# kernel's source file and the shared device header at capture time: a
-# changed source gives null (the counters may no longer describe the kernel).  The captures are summarised in
-# profiles/.
+# one ncu capture of the kernel on the workload, with the SHA-256 of the code
+# (comments removed, source_code_sha) of the kernel's file and the shared
+# device header at capture time: changed code gives null (the counters may no
+# longer describe the kernel).  The captures are summarised in profiles/.
 NCU_TRAFFIC = {
     # (kernel, storage, workload): (bytes per launch, source file,
-    # sha256 of that file followed by ct_internal.cuh at capture time)
+    # source_code_sha of that file and ct_internal.cuh at capture time)
     ("voxel_B", "f32", "cone_256"): (1211157504 + 80132096, "ct_backproject.cu",
-                                     "ac84394ba345b871dd74aedc2a9bb7e62298ef996fbeae6641737b7e64229022"),
+                                     "80ea43cf7db79703c3a6cf2f4ea2502d846665209df26d7877f6efafcc9137c5"),
     ("joseph_A", "f32", "cone_256"): (412163840 + 137549056, "ct_project.cu",
-                                      "c1b67033553caa0d83c0276ba58e3401460016ca6414d40ef57dac26541c49f8"),
+                                      "1433cf8b9c78380fe3e9b597dceeb3620d93fa4165fee657d0563f2d51c29e79"),
 }
 
 
@@ -231,28 +232,40 @@ NCU_TRAFFIC = {
 # at least 4 for B's 128-bit warp loads, 1 for A's 32-bit ones).  Keyed like NCU_TRAFFIC.
 NCU_L1 = {
     ("voxel_B", "f32", "cone_256"): ({"data_pipe_frac": 0.797, "passes_per_request": 5.34}, "ct_backproject.cu",
-                                     "ac84394ba345b871dd74aedc2a9bb7e62298ef996fbeae6641737b7e64229022"),
+                                     "80ea43cf7db79703c3a6cf2f4ea2502d846665209df26d7877f6efafcc9137c5"),
     ("joseph_A", "f32", "cone_256"): ({"data_pipe_frac": 0.452, "passes_per_request": 1.39}, "ct_project.cu",
-                                      "c1b67033553caa0d83c0276ba58e3401460016ca6414d40ef57dac26541c49f8"),
+                                      "1433cf8b9c78380fe3e9b597dceeb3620d93fa4165fee657d0563f2d51c29e79"),
 }
 
 
-def ncu_traffic(kernel, storage, workload, table=None):
+def source_code_sha(names):
+    """SHA-256 of the code of the given csrc files, comments and blank lines
+    removed: a capture stays keyed to the code it measured when only the
+    comments around it change."""
     import hashlib
+    csrc = os.path.join(ROOT, "paper_2201_07408_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(csrc, name), "r", encoding="utf-8") as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        lines = [ln.rstrip() for ln in text.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln).encode())
+    return h.hexdigest()
+
+
+def ncu_traffic(kernel, storage, workload, table=None):
     ent = (NCU_TRAFFIC if table is None else table).get((kernel, storage, workload))
     if not ent:
         return None
     nbytes, src, sha = ent
-    csrc = os.path.join(ROOT, "paper_2201_07408_gb300", "csrc")
-    h = hashlib.sha256()
     try:
         # the kernel's file and the shared device header it inlines
-        for name in (src, "ct_internal.cuh"):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+        code = source_code_sha((src, "ct_internal.cuh"))
     except OSError:
         return None
-    return nbytes if h.hexdigest() == sha else None
+    return nbytes if code == sha else None
 
 
 def measured_peaks():

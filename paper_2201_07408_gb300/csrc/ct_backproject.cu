@@ -9,9 +9,10 @@
 // GPU layout.  One thread owns a column (x, y) and a run of ZC consecutive
 // z; per view it computes W, M, u and the u-interpolation weights once and
 // then walks its z run with v affine in z.  The sinogram is read from a
-// copy with zero borders (PAD_U pixels along u, PAD_V rows along v): a view
-// whose u footprint misses the detector is skipped, and clamping the row
-// index into the border makes every other gather in bounds.
+// copy with zero borders (PAD_U pixels along u, padv rows along v): a view
+// whose u footprint misses the detector is skipped, and the host sizes the
+// row margin padv for the largest magnification over every slice computed,
+// so the row index needs no clamp (the checked build tests this per sample).
 #include <algorithm>
 
 #include "ct_internal.cuh"
