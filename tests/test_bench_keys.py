@@ -1,7 +1,6 @@
 """The bench's capture keys: the code hash ignores comments and blank lines
 and nothing else (CPU only)."""
 import os
-import shutil
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
