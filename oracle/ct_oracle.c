@@ -268,7 +268,11 @@ int or_s_row(const or_geom *g, long ray, long *idx, double *w)
         double am = 0.5 * (al[m] + al[m + 1]);
         long id[3];
         for (int a = 0; a < 3; ++a) {
-            double f = (S[a] + am * d[a] - lo[a]) / g->vox;
+            /* grid units measured from the centre: exact for a point at the
+             * centre (S = 0 on an axis the ray runs parallel to), so that a ray
+             * in the central plane of an even grid lies on the plane and goes
+             * to its positive side; (S - lo)/vox can round below the plane */
+            double f = (S[a] + am * d[a]) / g->vox + 0.5 * N[a];
             long i = (long)floor(f);
             if (i < 0) i = 0;
             if (i >= N[a]) i = N[a] - 1;

@@ -11,6 +11,8 @@ construction:
     quadrature of x along the ray (a voxel look-up per sample);
   * rays along a grid axis (2D, view angle 0) cross whole pixel columns:
     A_S x = vox times the column sum, exactly;
+  * a ray in the central boundary plane of an even grid lies in the
+    positive-side slice whatever the FP64 rounding of the grid origin;
   * A_S of a voxelised ellipsoid phantom converges to the closed-form line
     integrals as the grid is refined, and stays close to the Joseph A;
   * <A_S x, y> = <x, A_S^T y> to 1e-12.
@@ -121,6 +123,25 @@ def test_AS_axis_aligned_rays_sum_columns():
         col = math.floor((u + 0.5 * g.nx * g.vox) / g.vox)
         ref = g.vox * x[:, col].sum() if 0 <= col < g.nx else 0.0
         assert abs(y[iu] - ref) <= 1e-12 * max(1.0, abs(ref)), (iu, y[iu], ref)
+
+
+def test_AS_ray_in_the_central_plane_belongs_to_the_positive_side():
+    """Rays of the central detector row of a cone-beam scan lie in the plane
+    z = 0, which on a grid of even nz is the boundary between slices
+    nz/2 - 1 and nz/2; the reading for such a measure-zero case puts them in
+    slice nz/2 (the positive side).  With a voxel edge for which
+    (nz/2 vox)/vox rounds below nz/2 in FP64, every voxel of those rows must
+    still be in slice nz/2, with the whole chord length."""
+    vox = 2.6169519915633814
+    assert math.floor((0.5 * 28 * vox) / vox) == 13   # the rounding the reading must not depend on
+    g = ci._cone("central_plane", 0, vox, 4, 20, 9, 6.0, nxyz=(11, 9, 28), ang0=0.3)
+    ones = oracle.project_S(g, np.ones(g.n)).reshape(g.sino_shape)
+    for s in range(g.n_views):
+        for iu in range(g.nu):
+            ray = (s * g.nv + (g.nv - 1) // 2) * g.nu + iu
+            cols, lens = oracle.s_row(g, ray)
+            assert np.all(cols // (g.nx * g.ny) == g.nz // 2)
+            assert abs(lens.sum() - ones[s, (g.nv - 1) // 2, iu]) <= 1e-9
 
 
 def test_AS_converges_to_analytic_line_integrals_and_near_joseph():
