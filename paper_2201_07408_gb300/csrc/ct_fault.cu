@@ -136,10 +136,15 @@ ct_status ct_bounds_take(ct_geom *geom, unsigned long long *record)
     if (!geom || !record) return set_error(CT_EINVAL, "ct_bounds_take: null argument");
     *record = 0;
 #ifdef CT_CHECK_BOUNDS
-    cudaError_t e = cudaDeviceSynchronize();
+    // on the geometry's device, whichever is current
+    int prev = 0;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e == cudaSuccess && prev != geom->device) e = cudaSetDevice(geom->device);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess)
         e = cudaMemcpy(record, geom->g.bounds_word, sizeof(unsigned long long), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(geom->g.bounds_word, 0, sizeof(unsigned long long));
+    if (prev != geom->device) cudaSetDevice(prev);
     if (e != cudaSuccess) return cuda_error(e, "ct_bounds_take");
 #endif
     return CT_OK;
