@@ -437,7 +437,8 @@ CT_API const char *ct_fault_get(void);
 CT_API int ct_bounds_checked(void);
 
 /* Takes the geometry's first failed-check record and clears it, after the
- * device has finished all work (cudaDeviceSynchronize).  *record is 0 when
+ * geometry's device has finished all work (cudaDeviceSynchronize on it; the
+ * current device is left as it was).  *record is 0 when
  * no check failed (always in the regular build); otherwise
  *   bits 56..63  the site (1..6 above),
  *   bits 32..55  the view (sites 1-5) or z slice (site 6),
